@@ -1,0 +1,127 @@
+"""fp64 reference of the learned-bounds model (TEST INFRASTRUCTURE ONLY; see oracle/__init__).
+
+The paper accelerates ``A_P.lower_bound`` (Alg. 1) with a static S-tree over the key array
+(Sec. 2.1, "Storing P twice").  The GPU path replaces that search structure by a two-stage
+learned CDF model whose prediction is only a hint: every predicted position is verified and
+falls back to the full binary search, so the positions (and therefore the query results) are
+those of ``lower_bound`` by construction.  What needs a reference is the model itself:
+
+  root (a tiny monotone MLP, 1 -> H -> 1), on x = key / 2^60:
+      f(x) = c + sum_k exp(alpha_k) * sigmoid(exp(beta_k) * x + b_k)
+  trained to the normalised rank y = i / n of the sorted keys with the mean-squared error
+      L = (1/N) sum_i (f(x_i) - y_i)^2,
+  leaf j = clamp(floor(f(x) * J), 0, J - 1) for J leaves; each leaf is a least-squares line
+  of position against key offset; a per-leaf error window is the min and max of
+  (position - predicted position) over the leaf's keys.
+
+Nothing here is fitted to the GPU's fp32 numbers: the gradient is the analytic derivative of
+L, pinned by central finite differences in tests/test_oracle_learned.py, and the leaf fit is
+the closed-form normal equations, pinned against numpy.polyfit.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+KEY_SCALE = float(2 ** 60)  # x = key / 2^60 maps the 60-bit key space onto [0, 1)
+
+
+def unpack(theta: np.ndarray, H: int):
+    theta = np.asarray(theta, dtype=np.float64)
+    assert theta.shape == (3 * H + 1,)
+    return theta[0:H], theta[H:2 * H], theta[2 * H:3 * H], theta[3 * H]
+
+
+def pack(alpha, beta, b, c) -> np.ndarray:
+    return np.concatenate([np.asarray(alpha, np.float64), np.asarray(beta, np.float64),
+                           np.asarray(b, np.float64), np.asarray([c], np.float64)])
+
+
+def sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def root_forward(theta, x, H: int):
+    """f(x) of the root for fp64 inputs x (already scaled to [0, 1))."""
+    alpha, beta, b, c = unpack(theta, H)
+    x = np.asarray(x, np.float64)[:, None]
+    h = sigmoid(np.exp(beta)[None, :] * x + b[None, :])
+    return c + h @ np.exp(alpha)
+
+
+def root_loss(theta, x, y, H: int) -> float:
+    r = root_forward(theta, x, H) - np.asarray(y, np.float64)
+    return float(np.mean(r * r))
+
+
+def root_loss_grad(theta, x, y, H: int):
+    """Loss and its analytic gradient dL/dtheta, theta = (alpha, beta, b, c).
+
+    With r_i = 2 (f_i - y_i) / N, h_ik = sigmoid(exp(beta_k) x_i + b_k), A_k = exp(alpha_k):
+        dL/dc       = sum_i r_i
+        dL/dalpha_k = sum_i r_i A_k h_ik
+        dL/db_k     = sum_i r_i A_k h_ik (1 - h_ik)
+        dL/dbeta_k  = sum_i r_i A_k h_ik (1 - h_ik) exp(beta_k) x_i
+    """
+    alpha, beta, b, c = unpack(theta, H)
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    N = x.shape[0]
+    A = np.exp(alpha)
+    B = np.exp(beta)
+    h = sigmoid(B[None, :] * x[:, None] + b[None, :])
+    f = c + h @ A
+    res = f - y
+    loss = float(np.mean(res * res))
+    r = 2.0 * res / N
+    g_alpha = (r @ h) * A
+    s = h * (1.0 - h)
+    g_b = (r @ s) * A
+    g_beta = (r @ (s * x[:, None])) * A * B
+    g_c = float(np.sum(r))
+    return loss, pack(g_alpha, g_beta, g_b, g_c)
+
+
+def init_params(H: int) -> np.ndarray:
+    """Deterministic start: H logistic steps of equal height 1/H centred at (k + 1/2)/H with
+    slope 4H, i.e. close to the CDF of keys spread uniformly over the key space."""
+    k = np.arange(H, dtype=np.float64)
+    s = 4.0 * H
+    alpha = np.full(H, np.log(1.0 / H))
+    beta = np.full(H, np.log(s))
+    b = -s * (k + 0.5) / H
+    return pack(alpha, beta, b, 0.0)
+
+
+def adam_step(theta, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) with bias correction at step t >= 1."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    theta = theta - lr * mhat / (np.sqrt(vhat) + eps)
+    return theta, m, v
+
+
+def leaf_fit(u: np.ndarray, v: np.ndarray):
+    """Least-squares line v ~ slope * u + icpt by the normal equations (fp64).
+    Degenerate cases: no points -> (0, 0); all u equal -> (0, mean(v))."""
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    N = u.shape[0]
+    if N == 0:
+        return 0.0, 0.0
+    su, sv = u.sum(), v.sum()
+    suu, suv = (u * u).sum(), (u * v).sum()
+    den = N * suu - su * su
+    if den <= 0.0:
+        return 0.0, sv / N
+    slope = (N * suv - su * sv) / den
+    icpt = (sv - slope * su) / N
+    return float(slope), float(icpt)
+
+
+def error_window(positions: np.ndarray, predicted: np.ndarray):
+    """(min, max) of position - prediction over a leaf's keys: the window that contains the
+    true position of every key of the leaf."""
+    d = np.asarray(positions, np.int64) - np.asarray(predicted, np.int64)
+    return int(d.min()), int(d.max())

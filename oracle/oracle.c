@@ -1,0 +1,352 @@
+/*
+ * CPU oracle for batched 2-D distance reporting along a recursive space-filling curve
+ * ("Simpler is Faster", arXiv 2508.19891).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct statement of
+ * what the GPU path must compute.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load it.  It shares no code, header, table
+ * or constant with the CUDA library, and the CUDA library never calls it.
+ *
+ * Conventions (the paper's notation, with the readings used throughout the project):
+ *   - Domain D = [0, 2^w)^2 of integer points (the paper writes [1, 2^w], Sec. 2; the shift
+ *     by one is immaterial).  The GPU path fixes w = 30; the oracle takes w as a parameter
+ *     so that small grids can be enumerated exhaustively.
+ *   - pi(p) is a bit string of length 2w, stored in the low 2w bits of a uint64.
+ *   - Query (q, delta): integer centre q in D, integer radius delta >= 0.  The answer is the
+ *     closed ball {i : (x_i - q_x)^2 + (y_i - q_y)^2 <= delta^2} (problem statement, Sec. 2),
+ *     evaluated exactly in int64.
+ *
+ * Every function below cites the passage it follows.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORACLE_CURVE_Z 0
+#define ORACLE_CURVE_HILBERT 1
+
+/* ------------------------------------------------------------------------------------ */
+/* Keys.                                                                                 */
+/* ------------------------------------------------------------------------------------ */
+
+/* Z-curve (Morton) key, Alg. 2: bit 2i of the output is bit i of x, bit 2i+1 is bit i of y,
+ * for i in [w].  Written as the literal per-bit loop of the algorithm. */
+uint64_t oracle_key_z(uint32_t x, uint32_t y, int w)
+{
+    uint64_t out = 0;
+    for (int i = 0; i < w; ++i) {
+        uint64_t xi = (x >> i) & 1u;
+        uint64_t yi = (y >> i) & 1u;
+        out |= xi << (2 * i);
+        out |= yi << (2 * i + 1);
+    }
+    return out;
+}
+
+/* Hilbert key as a recursive space-filling curve (Sec. 2.1, "Choice of RSFC"; Def. 2.3).
+ * Orientation (the paper does not fix one): the order-1 curve visits
+ * (0,0) -> (0,1) -> (1,1) -> (1,0), i.e. the four quadrants get the 2-bit labels
+ * lower-left 00, upper-left 01, upper-right 10, lower-right 11 (Lemma 1 assigns suffixes
+ * 00,01,10,11 in visiting order).  Inside a quadrant the sub-square is mapped back to the
+ * base orientation before its own quadrant is read:
+ *   upper quadrants: unchanged;
+ *   lower-left:  reflected in the main diagonal (x and y exchanged);
+ *   lower-right: reflected in the anti-diagonal (x -> s-1-y, y -> s-1-x).
+ * The label of the parent is a prefix of the label of each child, as Def. 2.3 requires. */
+uint64_t oracle_key_h(uint32_t x, uint32_t y, int w)
+{
+    uint64_t key = 0;
+    uint64_t xx = x, yy = y;
+    for (int level = w - 1; level >= 0; --level) {
+        uint64_t s = (uint64_t)1 << level;           /* side of the sub-square */
+        int rx = (int)((xx >> level) & 1u);
+        int ry = (int)((yy >> level) & 1u);
+        int digit;
+        if (!rx && !ry) digit = 0;      /* lower-left  */
+        else if (!rx && ry) digit = 1;  /* upper-left  */
+        else if (rx && ry) digit = 2;   /* upper-right */
+        else digit = 3;                 /* lower-right */
+        key = (key << 2) | (uint64_t)digit;
+        /* coordinates inside the chosen sub-square */
+        xx &= s - 1;
+        yy &= s - 1;
+        if (!ry) {
+            if (rx) {   /* anti-diagonal reflection = point reflection followed by a swap */
+                xx = (s - 1) - xx;
+                yy = (s - 1) - yy;
+            }
+            uint64_t t = xx; xx = yy; yy = t;
+        }
+    }
+    return key;
+}
+
+uint64_t oracle_key(uint32_t x, uint32_t y, int w, int curve)
+{
+    return curve == ORACLE_CURVE_HILBERT ? oracle_key_h(x, y, w) : oracle_key_z(x, y, w);
+}
+
+/* pi(p) for every input point (Sec. 3.1.1: "compute the bit strings pi(A[i])"). */
+void oracle_keys(const int32_t* xy, uint64_t n, int w, int curve, uint64_t* keys)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        keys[i] = oracle_key((uint32_t)xy[2 * i], (uint32_t)xy[2 * i + 1], w, curve);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Construction: sort the points once by pi (Sec. 2, "store P in an array sorted by pi";  */
+/* Sec. 3.1.1).  Ties are broken by input index, which makes the order total.             */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct { uint64_t key; uint32_t id; } oracle_pair;
+
+static int pair_cmp(const void* a, const void* b)
+{
+    const oracle_pair* pa = (const oracle_pair*)a;
+    const oracle_pair* pb = (const oracle_pair*)b;
+    if (pa->key != pb->key) return pa->key < pb->key ? -1 : 1;
+    if (pa->id != pb->id) return pa->id < pb->id ? -1 : 1;
+    return 0;
+}
+
+/* Sort (key, id) pairs by key then id with the C library's qsort.
+ * Outputs: sorted keys, the input index of each sorted entry, and its coordinates. */
+int oracle_build(const int32_t* xy, uint64_t n, int w, int curve,
+                 uint64_t* skeys, uint32_t* sids, int32_t* sxy)
+{
+    oracle_pair* pairs = (oracle_pair*)malloc((n ? n : 1) * sizeof(oracle_pair));
+    if (!pairs) return -2;
+    for (uint64_t i = 0; i < n; ++i) {
+        pairs[i].key = oracle_key((uint32_t)xy[2 * i], (uint32_t)xy[2 * i + 1], w, curve);
+        pairs[i].id = (uint32_t)i;
+    }
+    qsort(pairs, n, sizeof(oracle_pair), pair_cmp);
+    for (uint64_t i = 0; i < n; ++i) {
+        skeys[i] = pairs[i].key;
+        sids[i] = pairs[i].id;
+        sxy[2 * i] = xy[2 * (uint64_t)pairs[i].id];
+        sxy[2 * i + 1] = xy[2 * (uint64_t)pairs[i].id + 1];
+    }
+    free(pairs);
+    return 0;
+}
+
+/* A_P.lower_bound (Alg. 1): first index x with keys[x] >= t, or n. */
+uint64_t oracle_lower_bound(const uint64_t* keys, uint64_t n, uint64_t t)
+{
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (keys[mid] < t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* cells(Q) (definition before Alg. 1) and the key interval of a cell (Observation).      */
+/* ------------------------------------------------------------------------------------ */
+
+/* Level l of the cells for a query radius delta: |.| is the side length, Q has side
+ * 2*delta, and cells(Q) takes the cells C with |Q| <= |C| < 2|Q|, i.e. the level l with
+ * 2*delta <= 2^l < 4*delta.  delta = 0 (Q is one point) takes the unit cells (l = 0).
+ * A level above w would be larger than the domain; it is capped at w. */
+int oracle_level(int64_t delta, int w)
+{
+    if (delta <= 0) return 0;
+    int l = 0;
+    while (((int64_t)1 << l) < 2 * delta) ++l;
+    return l < w ? l : w;
+}
+
+/* Writes the key intervals [lo, hi] of cells(Q) for Q = [q - delta, q + delta]^2 clipped
+ * to D, sorted by lo; returns how many (at most 4).  For a cell C at level l with lower-left
+ * grid point c, pi(C) is the common 2(w - l)-bit prefix of its points (Def. 2.3), so
+ * pi(C)o0 = (pi(c) >> 2l) << 2l and pi(C)o1 = pi(C)o0 + 4^l - 1 (Observation). */
+int oracle_cells(int32_t qx, int32_t qy, int32_t delta, int w, int curve,
+                 uint64_t lo[4], uint64_t hi[4], int* level_out)
+{
+    int64_t side = (int64_t)1 << w;
+    int64_t d = delta;
+    int64_t x0 = (int64_t)qx - d, x1 = (int64_t)qx + d;
+    int64_t y0 = (int64_t)qy - d, y1 = (int64_t)qy + d;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > side - 1) x1 = side - 1;
+    if (y1 > side - 1) y1 = side - 1;
+    int l = oracle_level(d, w);
+    if (level_out) *level_out = l;
+    int cnt = 0;
+    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
+        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
+            if (cnt == 4) return -1;   /* cannot happen: at most two cells per axis */
+            uint64_t corner = oracle_key((uint32_t)(cx << l), (uint32_t)(cy << l), w, curve);
+            uint64_t base = (l >= 32) ? 0 : ((corner >> (2 * l)) << (2 * l));
+            uint64_t span = (l >= 32) ? ~(uint64_t)0 : (((uint64_t)1 << (2 * l)) - 1);
+            lo[cnt] = base;
+            hi[cnt] = base + span;
+            ++cnt;
+        }
+    }
+    /* sort by lo (insertion sort of at most four entries) */
+    for (int i = 1; i < cnt; ++i) {
+        uint64_t a = lo[i], b = hi[i];
+        int j = i - 1;
+        while (j >= 0 && lo[j] > a) { lo[j + 1] = lo[j]; hi[j + 1] = hi[j]; --j; }
+        lo[j + 1] = a; hi[j + 1] = b;
+    }
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Query, Alg. 1: for each cell (in key order) lower_bound the start of its interval, scan */
+/* while the key is <= pi(C)o1 (inclusive end, Observation), and report every point with  */
+/* squared distance <= delta^2 (closed ball of the problem statement).                      */
+/* ------------------------------------------------------------------------------------ */
+
+static int query_valid(int32_t qx, int32_t qy, int32_t delta, int w)
+{
+    int64_t side = (int64_t)1 << w;
+    return qx >= 0 && qy >= 0 && (int64_t)qx < side && (int64_t)qy < side && delta >= 0;
+}
+
+/* Reports the hits of one query; writes them to out (if not NULL) and returns the count.
+ * scanned (if not NULL) receives the number of array entries visited. */
+static uint64_t query_one(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy,
+                          uint64_t n, int32_t qx, int32_t qy, int32_t delta, int w, int curve,
+                          uint32_t* out, uint64_t* scanned)
+{
+    if (!query_valid(qx, qy, delta, w)) { if (scanned) *scanned = 0; return 0; }
+    uint64_t lo[4], hi[4];
+    int cnt = oracle_cells(qx, qy, delta, w, curve, lo, hi, NULL);
+    int64_t d2 = (int64_t)delta * (int64_t)delta;
+    uint64_t k = 0, s = 0;
+    for (int c = 0; c < cnt; ++c) {
+        uint64_t x = oracle_lower_bound(skeys, n, lo[c]);
+        while (x < n && skeys[x] <= hi[c]) {
+            int64_t dx = (int64_t)sxy[2 * x] - qx;
+            int64_t dy = (int64_t)sxy[2 * x + 1] - qy;
+            if (dx * dx + dy * dy <= d2) {
+                if (out) out[k] = sids[x];
+                ++k;
+            }
+            ++x;
+            ++s;
+        }
+    }
+    if (scanned) *scanned = s;
+    return k;
+}
+
+typedef struct {
+    const uint64_t* skeys; const uint32_t* sids; const int32_t* sxy; uint64_t n;
+    const int32_t* q; const int32_t* delta; uint64_t m0, m1; int w, curve;
+    uint64_t* counts; const uint64_t* offsets; uint32_t* out_ids; uint64_t* scanned;
+} query_job;
+
+static void* query_worker(void* arg)
+{
+    query_job* j = (query_job*)arg;
+    for (uint64_t i = j->m0; i < j->m1; ++i) {
+        uint32_t* out = j->out_ids ? j->out_ids + j->offsets[i] : NULL;
+        uint64_t s = 0;
+        uint64_t k = query_one(j->skeys, j->sids, j->sxy, j->n, j->q[2 * i], j->q[2 * i + 1],
+                               j->delta[i], j->w, j->curve, out, &s);
+        if (j->counts) j->counts[i] = k;
+        if (j->scanned) j->scanned[i] = s;
+    }
+    return NULL;
+}
+
+/* Runs the queries [0, m) on `threads` host threads, each taking a contiguous block of
+ * queries.  With out_ids == NULL only counts (and scanned) are produced; otherwise the ids of
+ * query i are written at out_ids[offsets[i] ...].  Queries are independent, so the split
+ * does not change any result. */
+int oracle_query(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy, uint64_t n,
+                 const int32_t* q, const int32_t* delta, uint64_t m, int w, int curve,
+                 uint64_t* counts, const uint64_t* offsets, uint32_t* out_ids,
+                 uint64_t* scanned, int threads)
+{
+    if (threads < 1) threads = 1;
+    if ((uint64_t)threads > m) threads = (int)(m ? m : 1);
+    query_job* jobs = (query_job*)calloc((size_t)threads, sizeof(query_job));
+    pthread_t* tids = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tids) { free(jobs); free(tids); return -2; }
+    for (int t = 0; t < threads; ++t) {
+        query_job* j = &jobs[t];
+        j->skeys = skeys; j->sids = sids; j->sxy = sxy; j->n = n;
+        j->q = q; j->delta = delta; j->w = w; j->curve = curve;
+        j->m0 = m * (uint64_t)t / (uint64_t)threads;
+        j->m1 = m * (uint64_t)(t + 1) / (uint64_t)threads;
+        j->counts = counts; j->offsets = offsets; j->out_ids = out_ids; j->scanned = scanned;
+    }
+    if (threads == 1) {
+        query_worker(&jobs[0]);
+    } else {
+        for (int t = 0; t < threads; ++t) pthread_create(&tids[t], NULL, query_worker, &jobs[t]);
+        for (int t = 0; t < threads; ++t) pthread_join(tids[t], NULL);
+    }
+    free(jobs);
+    free(tids);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Brute force over the unsorted input: the problem statement of Sec. 2 taken literally.  */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    const int32_t* xy; uint64_t n; const int32_t* q; const int32_t* delta;
+    uint64_t m0, m1; int w; uint64_t* counts; const uint64_t* offsets; uint32_t* out_ids;
+} brute_job;
+
+static void* brute_worker(void* arg)
+{
+    brute_job* j = (brute_job*)arg;
+    for (uint64_t i = j->m0; i < j->m1; ++i) {
+        int32_t qx = j->q[2 * i], qy = j->q[2 * i + 1], dl = j->delta[i];
+        uint64_t k = 0;
+        if (query_valid(qx, qy, dl, j->w)) {
+            int64_t d2 = (int64_t)dl * (int64_t)dl;
+            for (uint64_t p = 0; p < j->n; ++p) {
+                int64_t dx = (int64_t)j->xy[2 * p] - qx;
+                int64_t dy = (int64_t)j->xy[2 * p + 1] - qy;
+                if (dx * dx + dy * dy <= d2) {
+                    if (j->out_ids) j->out_ids[j->offsets[i] + k] = (uint32_t)p;
+                    ++k;
+                }
+            }
+        }
+        if (j->counts) j->counts[i] = k;
+    }
+    return NULL;
+}
+
+/* Per-query hits in ascending input index (not key) order. */
+int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t* delta,
+                 uint64_t m, int w, uint64_t* counts, const uint64_t* offsets,
+                 uint32_t* out_ids, int threads)
+{
+    if (threads < 1) threads = 1;
+    if ((uint64_t)threads > m) threads = (int)(m ? m : 1);
+    brute_job* jobs = (brute_job*)calloc((size_t)threads, sizeof(brute_job));
+    pthread_t* tids = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tids) { free(jobs); free(tids); return -2; }
+    for (int t = 0; t < threads; ++t) {
+        brute_job* j = &jobs[t];
+        j->xy = xy; j->n = n; j->q = q; j->delta = delta; j->w = w;
+        j->m0 = m * (uint64_t)t / (uint64_t)threads;
+        j->m1 = m * (uint64_t)(t + 1) / (uint64_t)threads;
+        j->counts = counts; j->offsets = offsets; j->out_ids = out_ids;
+    }
+    if (threads == 1) {
+        brute_worker(&jobs[0]);
+    } else {
+        for (int t = 0; t < threads; ++t) pthread_create(&tids[t], NULL, brute_worker, &jobs[t]);
+        for (int t = 0; t < threads; ++t) pthread_join(tids[t], NULL);
+    }
+    free(jobs);
+    free(tids);
+    return 0;
+}

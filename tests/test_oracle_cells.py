@@ -1,0 +1,91 @@
+"""Pins for cells(Q) (definition before Alg. 1) and the Observation's key interval.
+
+Exhaustive over every query centre and radius of small grids: at most four cells
+(Sec. 1.2, 2^d with d = 2), cell size |Q| <= |C| < 2|Q| with |.| the side, coverage of every
+grid point of Q, disjointness, and that each cell meets Q.  Special cases: delta = 0 gives
+the point's own unit interval, a radius of at least half the domain gives the whole domain.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _grid_keys(w, curve):
+    side = 1 << w
+    f = oracle.key_z if curve == "z" else oracle.key_h
+    return np.array([[f(x, y, w) for x in range(side)] for y in range(side)], dtype=np.int64)
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("w", [3, 4])
+def test_cells_exhaustive(curve, w):
+    side = 1 << w
+    keys = _grid_keys(w, curve)
+    for qy in range(side):
+        for qx in range(side):
+            for delta in range(0, 2 * side + 1):
+                rngs, l = oracle.cells(qx, qy, delta, w, curve)
+                assert 1 <= len(rngs) <= 4
+                # level: 2*delta <= 2^l < 4*delta (capped at w); delta = 0 -> l = 0
+                if delta == 0:
+                    assert l == 0
+                elif l < w:
+                    assert 2 * delta <= (1 << l) < 4 * delta
+                else:
+                    assert (1 << w) < 4 * delta
+                for lo, hi in rngs:
+                    assert hi - lo + 1 == 4 ** l
+                    assert lo % (4 ** l) == 0
+                # sorted and disjoint
+                for (a, b), (c, d) in zip(rngs, rngs[1:]):
+                    assert b < c
+                x0, x1 = max(0, qx - delta), min(side - 1, qx + delta)
+                y0, y1 = max(0, qy - delta), min(side - 1, qy + delta)
+                inq = keys[y0:y1 + 1, x0:x1 + 1].ravel()
+                # coverage: every grid point of Q has its key inside some interval
+                covered = np.zeros(inq.shape, bool)
+                for lo, hi in rngs:
+                    covered |= (inq >= lo) & (inq <= hi)
+                assert covered.all()
+                # every cell meets Q
+                for lo, hi in rngs:
+                    assert ((inq >= lo) & (inq <= hi)).any()
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+def test_cells_same_total_length(curve):
+    """Both curves label the same quadtree cells, so the covered key length agrees."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        qx, qy = (int(v) for v in rng.integers(0, 1 << 30, size=2))
+        delta = int(rng.integers(0, 1 << 24))
+        rz, lz = oracle.cells(qx, qy, delta, 30, "z")
+        rh, lh = oracle.cells(qx, qy, delta, 30, "h")
+        assert lz == lh and len(rz) == len(rh)
+        assert sum(b - a + 1 for a, b in rz) == sum(b - a + 1 for a, b in rh)
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+def test_cells_special_cases_w30(curve):
+    f = oracle.key_z if curve == "z" else oracle.key_h
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        qx, qy = (int(v) for v in rng.integers(0, 1 << 30, size=2))
+        r, l = oracle.cells(qx, qy, 0, 30, curve)
+        k = f(qx, qy, 30)
+        assert l == 0 and r == [(k, k)]
+        r, l = oracle.cells(qx, qy, 1 << 29, 30, curve)
+        assert l == 30 and r == [(0, (1 << 60) - 1)]
+        r, l = oracle.cells(qx, qy, 2 ** 31 - 1, 30, curve)
+        assert l == 30 and r == [(0, (1 << 60) - 1)]
+
+
+def test_level_values():
+    assert oracle.level(0) == 0
+    assert oracle.level(1) == 1        # 2 <= 2 < 4
+    assert oracle.level(2) == 2        # 4 <= 4 < 8
+    assert oracle.level(3) == 3        # 6 <= 8 < 12
+    assert oracle.level(8366) == 15    # 16732 <= 32768 < 33464
+    assert oracle.level((1 << 28) + 1) == 30
+    assert oracle.level(1 << 28) == 29

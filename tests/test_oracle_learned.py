@@ -1,0 +1,72 @@
+"""Pins for the fp64 reference of the learned-bounds model: the analytic gradient against
+central finite differences, the Adam step against its closed form at t = 1, and the leaf fit
+against numpy.polyfit and exact lines."""
+import numpy as np
+import pytest
+
+from oracle import learned as L
+
+
+@pytest.mark.parametrize("H", [1, 4, 16])
+def test_gradient_vs_finite_differences(H):
+    rng = np.random.default_rng(H)
+    x = np.sort(rng.uniform(0, 1, 300))
+    y = np.linspace(0, 1, 300)
+    theta = L.init_params(H) + rng.normal(0, 0.3, 3 * H + 1)
+    loss, g = L.root_loss_grad(theta, x, y, H)
+    assert loss == pytest.approx(L.root_loss(theta, x, y, H), rel=1e-12)
+    eps = 1e-6
+    fd = np.empty_like(theta)
+    for i in range(theta.size):
+        tp = theta.copy(); tp[i] += eps
+        tm = theta.copy(); tm[i] -= eps
+        fd[i] = (L.root_loss(tp, x, y, H) - L.root_loss(tm, x, y, H)) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_zero_loss_at_exact_fit():
+    H = 3
+    theta = L.init_params(H)
+    x = np.linspace(0, 1, 50)
+    y = L.root_forward(theta, x, H)
+    loss, g = L.root_loss_grad(theta, x, y, H)
+    assert loss == 0.0 and np.all(g == 0.0)
+
+
+def test_root_is_monotone():
+    H = 8
+    rng = np.random.default_rng(0)
+    theta = L.init_params(H) + rng.normal(0, 1.0, 3 * H + 1)
+    x = np.linspace(0, 1, 10001)
+    assert np.all(np.diff(L.root_forward(theta, x, H)) >= 0)
+
+
+def test_adam_first_step_closed_form():
+    """At t = 1 the bias-corrected moments are g and g^2, so the step is lr*g/(|g|+eps)."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    th = np.zeros(4)
+    th1, m, v = L.adam_step(th, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    np.testing.assert_allclose(th1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_leaf_fit():
+    rng = np.random.default_rng(2)
+    u = rng.uniform(0, 1e12, 500)
+    v = 3e-9 * u + 17.0 + rng.normal(0, 2.0, 500)
+    s, c = L.leaf_fit(u, v)
+    ps, pc = np.polyfit(u, v, 1)
+    assert s == pytest.approx(ps, rel=1e-9) and c == pytest.approx(pc, rel=1e-9, abs=1e-6)
+    s, c = L.leaf_fit(np.arange(10.0), 2.0 * np.arange(10.0) + 5.0)
+    assert s == pytest.approx(2.0) and c == pytest.approx(5.0)
+    assert L.leaf_fit(np.array([]), np.array([])) == (0.0, 0.0)
+    assert L.leaf_fit(np.full(4, 7.0), np.arange(4.0)) == (0.0, 1.5)
+
+
+def test_error_window_contains_all():
+    pos = np.arange(100)
+    pred = pos + np.random.default_rng(1).integers(-5, 6, 100)
+    lo, hi = L.error_window(pos, pred)
+    assert np.all(pos - pred >= lo) and np.all(pos - pred <= hi)
+    assert lo == (pos - pred).min() and hi == (pos - pred).max()
