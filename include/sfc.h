@@ -1,0 +1,241 @@
+/*
+ * sfc.h — C ABI of the GB300 (sm_103a) library for batched 2-D distance reporting over a
+ * point set sorted along a space-filling curve (method of "Simpler is Faster: Practical
+ * Distance Reporting by Sorting Along a Space-Filling Curve", arXiv 2508.19891).
+ *
+ * Problem (Sec. 2, problem statement): store a set P of integer points so that a query
+ * (q, delta) returns every point of P within distance delta of q.  Method (Sec. 2, Alg. 1):
+ * sort P by its curve key pi(p); a query becomes at most four contiguous key intervals
+ * (cells(Q), Observation), each located by lower_bound and scanned with an exact filter.
+ *
+ * Conventions for every call:
+ *   - Coordinates are int32 in [0, 2^30) (w = 30 bits per axis); keys are the 60-bit curve
+ *     labels of Def. 2.3 in a uint64.  Points and queries are interleaved (x, y) pairs.
+ *   - Radii are int32 >= 0.  A point i is reported for (q, delta) iff
+ *     (x_i - q_x)^2 + (y_i - q_y)^2 <= delta^2, evaluated exactly in 64-bit integers
+ *     (the closed ball B_delta(q) of the problem statement).
+ *   - Ids are input indices (0-based); points added by sfc_update get fresh ids.
+ *   - "d_" arguments are DEVICE pointers on the index's device, "h_" arguments HOST
+ *     pointers.  The caller owns every buffer it passes; nothing is retained after the call
+ *     except inside the opaque index.  All device work is enqueued on `stream` (a
+ *     cudaStream_t; NULL = the legacy default stream) and is asynchronous unless a call says
+ *     it synchronises.
+ *   - Host-detectable argument errors are returned at once and enqueue nothing.  Errors
+ *     found on the device (a coordinate outside the domain, a negative radius, output
+ *     capacity exceeded, a look-back wait that gave up) are recorded in the index's device
+ *     status word and reported by sfc_device_status() or by the next call that synchronises.
+ *     No call traps or aborts.
+ *   - Nothing falls back to the CPU: every step of every call runs in this library's CUDA
+ *     kernels.
+ */
+#ifndef SFC_H
+#define SFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFC_OK = 0,
+    SFC_ERR_INVALID = -1,    /* bad argument, or (device) bad coordinate / radius */
+    SFC_ERR_OOM = -2,        /* device allocation failed */
+    SFC_ERR_CAPACITY = -3,   /* output capacity smaller than the result; offsets are complete */
+    SFC_ERR_NOT_FOUND = -4,  /* update deletes an id that is not live (batch not applied) */
+    SFC_ERR_TIMEOUT = -5,    /* a bounded device wait gave up; results of that call are void */
+    SFC_ERR_CUDA = -6,       /* a CUDA runtime call failed */
+    SFC_ERR_STATE = -7       /* call out of order (e.g. sfc_query_write without a count) */
+} sfc_status;
+
+typedef enum { SFC_CURVE_Z = 0, SFC_CURVE_HILBERT = 1 } sfc_curve;
+typedef enum { SFC_BOUNDS_BINARY = 0, SFC_BOUNDS_LEARNED = 1 } sfc_bounds;
+
+/* Device status bits (sfc_device_status_bits). */
+#define SFC_DEV_BAD_POINT   0x1u   /* a point coordinate outside [0, 2^30) */
+#define SFC_DEV_BAD_QUERY   0x2u   /* a query centre outside the domain or a radius < 0 */
+#define SFC_DEV_CAPACITY    0x4u   /* sfc_query_* output capacity exceeded */
+#define SFC_DEV_TIMEOUT     0x8u   /* a look-back or work-queue wait hit its iteration limit */
+#define SFC_DEV_NOT_FOUND   0x10u  /* sfc_update: delete of a non-live or duplicate id */
+
+typedef struct sfc_index sfc_index;   /* opaque; owned by the library */
+
+typedef struct {
+    sfc_bounds bounds;      /* bound search used by queries (default SFC_BOUNDS_BINARY) */
+    int leaves;             /* learned model: number of leaf segments (default 4096) */
+    int train_steps;        /* learned model: Adam steps of the root (default 300) */
+    int train_samples;      /* learned model: keys sampled for root training (default 65536) */
+    float learning_rate;    /* learned model: Adam step size (default 0.02) */
+    int chunk;              /* scan chunk in points (0 = autotuned/default 1024) */
+    int mask_budget_mb;     /* device memory for hit masks of the two-pass scan (default 1024) */
+    int reorder_queries;    /* 1 = process queries in curve order for cache reuse (default 1) */
+} sfc_options;
+
+/* Fills *opt with the defaults listed above. */
+void sfc_default_options(sfc_options* opt);
+
+/* ---------------------------------------------------------------------------------- */
+/* Index construction (Sec. 2: "store P in an array sorted by pi(p)"; Sec. 3.1.1:      */
+/* compute the keys and sort once).                                                     */
+/* ---------------------------------------------------------------------------------- */
+
+/* Builds an index over n points d_points (int32[n][2], device).  Keys of `curve`, then a
+ * stable LSD radix sort of (key, id); the sorted coordinates are written alongside.
+ * If opt->bounds is SFC_BOUNDS_LEARNED the learned model is trained as well.
+ * n may be 0; n must be < 2^32 - 1.  *out receives the new index (NULL on error).
+ * Errors: SFC_ERR_INVALID (NULL out, n too large, unknown curve), SFC_ERR_OOM,
+ * SFC_ERR_CUDA.  Bad coordinates set SFC_DEV_BAD_POINT (keys of such points are
+ * unspecified). */
+sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
+                     const sfc_options* opt, void* stream);
+
+/* As sfc_build with the points in host memory (copied inside the call). */
+sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, sfc_curve curve,
+                          const sfc_options* opt, void* stream);
+
+/* Frees the index and everything it owns (stream-ordered on the stream of the last call). */
+void sfc_destroy(sfc_index* idx);
+
+/* ---------------------------------------------------------------------------------- */
+/* Queries (Alg. 1 for a batch).                                                        */
+/* ---------------------------------------------------------------------------------- */
+
+/* Counting half of a query batch.  d_q: int32[m][2] centres, d_delta: int32[m] radii.
+ * Writes d_out_offsets (uint64[m+1], device): out_offsets[i] is where query i's ids start,
+ * out_offsets[m] the total.  Keeps the batch's plan in the index so that sfc_query_write
+ * can emit the ids without redoing the search or the count.  Invalid queries (centre outside
+ * the domain, radius < 0) report nothing and set SFC_DEV_BAD_QUERY. */
+sfc_status sfc_query_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
+                           uint64_t m, uint64_t* d_out_offsets, void* stream);
+
+/* Writing half: must follow sfc_query_count on the same index with the same d_q, d_delta,
+ * m and d_out_offsets (else SFC_ERR_STATE).  Writes the ids of query i to
+ * d_out_ids[out_offsets[i] .. out_offsets[i+1]) in ascending (key, id) order.  Ids whose
+ * slot is >= ids_capacity are not written and SFC_DEV_CAPACITY is set. */
+sfc_status sfc_query_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
+                           uint64_t m, const uint64_t* d_out_offsets, uint32_t* d_out_ids,
+                           uint64_t ids_capacity, void* stream);
+
+/* Both halves in one asynchronous call (capacity mode; capturable in a CUDA graph once
+ * sfc_reserve_queries has sized the workspace for m). */
+sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
+                           uint64_t m, uint64_t* d_out_offsets, uint32_t* d_out_ids,
+                           uint64_t ids_capacity, void* stream);
+
+/* Whole query batch with host buffers: copies h_q/h_delta in, runs the batch, copies
+ * h_out_offsets (uint64[m+1]) and the ids back.  Synchronises `stream`.  If the total
+ * exceeds ids_capacity, only h_out_offsets is written and SFC_ERR_CAPACITY is returned. */
+sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta,
+                                uint64_t m, uint64_t* h_out_offsets, uint32_t* h_out_ids,
+                                uint64_t ids_capacity, void* stream);
+
+/* Pre-sizes the query workspace for batches of up to m queries, so that later query calls
+ * allocate nothing (needed before capturing them in a CUDA graph). */
+sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream);
+
+/* Chooses the bound search of later queries.  SFC_BOUNDS_LEARNED requires a trained model
+ * (sfc_train_model or opt->bounds at build), else SFC_ERR_STATE. */
+sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);
+
+/* ---------------------------------------------------------------------------------- */
+/* Learned bounds: two-stage CDF model replacing the search tree over the keys          */
+/* (Sec. 2.1 "Storing P twice" uses a static B-tree; this library learns the CDF).      */
+/* ---------------------------------------------------------------------------------- */
+
+/* (Re)trains the model on the index's sorted keys: the root MLP by Adam on the GPU, then
+ * the leaf least-squares lines and the exact per-leaf error windows. */
+sfc_status sfc_train_model(sfc_index* idx, void* stream);
+
+/* Number of root hidden units H; the root has 3H + 1 parameters (alpha[H], beta[H], b[H], c). */
+int sfc_model_hidden(void);
+
+/* Loss and gradient of the root for given parameters on given samples (the training kernels
+ * run once, no update): h_params float[3H+1] (host), d_keys uint64[s] (device, sample keys),
+ * d_y float[s] (device, target normalised ranks).  Writes *h_loss and h_grad float[3H+1]
+ * (host).  Synchronises `stream`. */
+sfc_status sfc_model_loss_grad(const float* h_params, const uint64_t* d_keys, const float* d_y,
+                               uint64_t s, float* h_loss, float* h_grad, void* stream);
+
+/* One Adam step of the device optimiser on host-given state (for tests): updates h_params,
+ * h_m, h_v (float[3H+1] each) in place with gradient h_grad at step t >= 1. */
+sfc_status sfc_model_adam_step(float* h_params, float* h_m, float* h_v, const float* h_grad,
+                               int t, float lr, void* stream);
+
+/* Copies the trained model out (host): root parameters float[3H+1]; per leaf j < leaves:
+ * first position, end position, slope, intercept, err_lo, err_hi.  Any pointer may be NULL.
+ * *h_leaves receives the leaf count.  Synchronises. */
+sfc_status sfc_model_get(const sfc_index* idx, float* h_params, int* h_leaves,
+                         uint32_t* h_first, uint32_t* h_end, float* h_slope, float* h_icpt,
+                         int32_t* h_err_lo, int32_t* h_err_hi, void* stream);
+
+/* Statistics of the last learned-bounds query batch: endpoints searched, endpoints whose
+ * window missed (fell back to full binary search), and the sum of window lengths.
+ * Synchronises. */
+sfc_status sfc_model_stats(const sfc_index* idx, uint64_t* h_endpoints, uint64_t* h_misses,
+                           uint64_t* h_window_sum, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Dynamic setting (Sec. 2.1 "Dynamic implementation"; Sec. 3.3), batched.              */
+/* ---------------------------------------------------------------------------------- */
+
+/* Applies one batch: deletes d_delete_ids (uint32[k_del], device) first, then inserts
+ * d_inserts (int32[k_ins][2], device) with ids first_new_id, first_new_id + 1, ...
+ * (written to *h_first_new_id; ids are never reused).  The sorted arrays become those of a
+ * rebuild from scratch over the live set; a trained model is refitted.  Synchronises
+ * `stream` to validate the deletes: a delete of a non-live or repeated id returns
+ * SFC_ERR_NOT_FOUND and changes nothing. */
+sfc_status sfc_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins,
+                      const uint32_t* d_delete_ids, uint64_t k_del, uint32_t* h_first_new_id,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Introspection and individual steps (used by the parity tests).                       */
+/* ---------------------------------------------------------------------------------- */
+
+/* Device views of the sorted arrays (owned by the index; valid until the next
+ * sfc_update/sfc_destroy): keys uint64[n], ids uint32[n], xy int32[n][2]. */
+sfc_status sfc_get_sorted(const sfc_index* idx, const uint64_t** d_keys, const uint32_t** d_ids,
+                          const int32_t** d_xy, uint64_t* n);
+
+/* Synchronises `stream`, returns the device status word accumulated since the last call
+ * in *h_bits (SFC_DEV_* bits) and clears it.  Returns the sfc_status of the most severe
+ * bit (SFC_OK if none). */
+sfc_status sfc_device_status(sfc_index* idx, uint32_t* h_bits, void* stream);
+
+/* Curve keys of n points (Alg. 2 for Z; the Hilbert labelling of Sec. 2.1), device in/out. */
+sfc_status sfc_keys(const int32_t* d_points, uint64_t n, sfc_curve curve, uint64_t* d_keys,
+                    void* stream);
+
+/* Inverse of sfc_keys: coordinates of n keys (device in/out). */
+sfc_status sfc_decode(const uint64_t* d_keys, uint64_t n, sfc_curve curve, int32_t* d_points,
+                      void* stream);
+
+/* Stable sort of (key, id) pairs by key with the library's onesweep radix sort: d_keys_in
+ * uint64[n], d_ids_in uint32[n] (NULL = ids 0..n-1), outputs d_keys_out / d_ids_out
+ * (must not alias the inputs).  Allocates and frees its own workspace on `stream`. */
+sfc_status sfc_sort_pairs(const uint64_t* d_keys_in, const uint32_t* d_ids_in, uint64_t n,
+                          uint64_t* d_keys_out, uint32_t* d_ids_out, void* stream);
+
+/* Exclusive prefix sum of n uint32 into uint64[n+1] (the last entry is the total). */
+sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
+
+/* Ranges and bounds of a query batch (Alg. 1 lines 1-4): for each query i, up to four
+ * merged key intervals of cells(Q) (d_lo/d_hi uint64[4m], unused slots lo = 1, hi = 0) and
+ * their array bounds by the index's current bound search (d_begin/d_end uint32[4m]);
+ * d_count uint32[m] receives the number of intervals. Any output may be NULL. */
+sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
+                            uint64_t m, uint64_t* d_lo, uint64_t* d_hi, uint32_t* d_begin,
+                            uint32_t* d_end, uint32_t* d_count, void* stream);
+
+/* Number of this library's kernels launched by this process so far (host counter). */
+uint64_t sfc_launch_count(void);
+
+/* Human-readable name of a status code. */
+const char* sfc_status_string(sfc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFC_H */

@@ -1,0 +1,468 @@
+// C ABI of the library (include/sfc.h): argument checks, the index object and its
+// workspaces, and the order of kernel launches for each call.  No computation of the method
+// happens here; every step runs in the kernels of keygen.cu, radix.cu, scan.cu, query.cu,
+// learned.cu and update.cu.
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sfc_internal.cuh"
+#include "query.cuh"
+#include "index.cuh"
+
+namespace sfc {
+
+std::atomic<uint64_t> g_launches{0};
+
+int num_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
+    }
+    return SFC_OK;
+}
+
+void dev_free(void* p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
+}  // namespace sfc
+
+using namespace sfc;
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+sfc_status ensure_status_buf(sfc_index* idx, cudaStream_t st)
+{
+    if (idx->status.ptr) return SFC_OK;
+    SFC_TRY(idx->status.ensure(sizeof(uint32_t) * 4 + sizeof(unsigned long long) * 4, st));
+    SFC_CUDA_TRY(cudaMemsetAsync(idx->status.ptr, 0, idx->status.bytes, st));
+    return SFC_OK;
+}
+
+uint32_t* status_word(sfc_index* idx) { return idx->status.as<uint32_t>(); }
+unsigned long long* model_stats(sfc_index* idx)
+{
+    return reinterpret_cast<unsigned long long*>(idx->status.as<unsigned char>() + 16);
+}
+
+sfc_status build_from_device(sfc_index* idx, const int32_t* d_points, cudaStream_t st)
+{
+    const uint64_t n = idx->n;
+    SFC_TRY(idx->keys.ensure(n * sizeof(uint64_t), st));
+    SFC_TRY(idx->ids.ensure(n * sizeof(uint32_t), st));
+    SFC_TRY(idx->xy.ensure(n * sizeof(int2), st));
+    SortSource src;
+    src.points = reinterpret_cast<const int2*>(d_points);
+    src.curve = idx->curve;
+    SortDest dst;
+    dst.keys = idx->keys.as<uint64_t>();
+    dst.vals = idx->ids.as<uint32_t>();
+    dst.xy = idx->xy.as<int2>();
+    dst.curve = idx->curve;
+    SFC_TRY(radix_sort(src, n, dst, idx->sort_ws, status_word(idx), st));
+    // the id -> coordinates table of the dynamic setting starts as a copy of the input
+    SFC_TRY(idx->xy_by_id.ensure(n * sizeof(int2), st));
+    if (n) SFC_CUDA_TRY(cudaMemcpyAsync(idx->xy_by_id.ptr, d_points, n * sizeof(int2),
+                                        cudaMemcpyDeviceToDevice, st));
+    idx->next_id = (uint32_t)n;
+    SFC_TRY(ensure_alive_bits(idx, n, st));
+    return SFC_OK;
+}
+
+QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint64_t m)
+{
+    QueryArgs a{};
+    a.curve = idx->curve;
+    a.keys = idx->keys.as<uint64_t>();
+    a.ids = idx->ids.as<uint32_t>();
+    a.xy = idx->xy.as<int2>();
+    a.n = (uint32_t)idx->n;
+    a.q = q;
+    a.delta = delta;
+    a.m = m;
+    a.status = status_word(idx);
+    return a;
+}
+
+sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
+{
+    QueryWs& w = idx->qws;
+    SFC_TRY(w.ranges.ensure(m * 8 * sizeof(uint32_t), st));
+    SFC_TRY(w.nchunks.ensure(m * sizeof(uint32_t), st));
+    SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
+    SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
+    SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
+    const uint64_t budget = (uint64_t)idx->opt.mask_budget_mb << 20;
+    uint64_t want = m * 4096ull + (1ull << 20);
+    if (want > budget) want = budget;
+    if (w.masks.bytes < want) SFC_TRY(w.masks.ensure(want, st));
+    return SFC_OK;
+}
+
+const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
+{
+    if (idx->bounds != SFC_BOUNDS_LEARNED || !idx->model.trained) return nullptr;
+    v.root = idx->model.root;
+    v.leaf = idx->model.leaves.as<LeafParams>();
+    v.stats = model_stats(idx);
+    return &v;
+}
+
+sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                    uint64_t* d_out_offsets, cudaStream_t st)
+{
+    SFC_TRY(ensure_status_buf(idx, st));
+    if (m == 0) {
+        SFC_CUDA_TRY(cudaMemsetAsync(d_out_offsets, 0, sizeof(uint64_t), st));
+        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0};
+        return SFC_OK;
+    }
+    SFC_TRY(ensure_query_ws(idx, m, st));
+    QueryWs& w = idx->qws;
+    QueryArgs a = base_args(idx, d_q, d_delta, m);
+    a.ranges = w.ranges.as<uint32_t>();
+    a.nchunks = w.nchunks.as<uint32_t>();
+    a.chunk_base = w.chunk_base.as<uint64_t>();
+    a.counts = w.counts.as<uint32_t>();
+    a.masks = w.masks.as<uint32_t>();
+    a.chunk = idx->chunk;
+    a.mask_chunks = w.masks.bytes / (a.chunk / 8);
+    a.batch = idx->batch;
+    a.qbatch = idx->qbatch;
+    a.work_ctr = w.ctr.as<unsigned long long>();
+    a.out_offsets = d_out_offsets;
+    SFC_CUDA_TRY(cudaMemsetAsync(a.counts, 0, m * sizeof(uint32_t), st));
+    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, 4 * sizeof(unsigned long long), st));
+    LearnedModelView lv;
+    SFC_TRY(launch_plan(a, model_view(idx, lv), st));
+    SFC_TRY(exclusive_scan_u32(a.nchunks, m, a.chunk_base, idx->scan_ws, a.status, st));
+    SFC_TRY(launch_count(a, st));
+    SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
+    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk};
+    return SFC_OK;
+}
+
+sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                    const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t cap, cudaStream_t st)
+{
+    QueryWs& w = idx->qws;
+    if (!w.pending.valid || w.pending.q != d_q || w.pending.delta != d_delta || w.pending.m != m ||
+        w.pending.offsets != d_out_offsets)
+        return SFC_ERR_STATE;
+    w.pending.valid = false;
+    if (m == 0) return SFC_OK;
+    QueryArgs a = base_args(idx, d_q, d_delta, m);
+    a.ranges = w.ranges.as<uint32_t>();
+    a.nchunks = w.nchunks.as<uint32_t>();
+    a.chunk_base = w.chunk_base.as<uint64_t>();
+    a.counts = w.counts.as<uint32_t>();
+    a.masks = w.masks.as<uint32_t>();
+    a.chunk = w.pending.chunk;
+    a.mask_chunks = w.masks.bytes / (a.chunk / 8);
+    a.batch = idx->batch;
+    a.qbatch = idx->qbatch;
+    a.work_ctr = w.ctr.as<unsigned long long>();
+    a.out_offsets = const_cast<uint64_t*>(d_out_offsets);
+    a.out_ids = d_out_ids;
+    a.ids_capacity = d_out_ids ? cap : 0;
+    return launch_write(a, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sfc_default_options(sfc_options* opt)
+{
+    if (!opt) return;
+    opt->bounds = SFC_BOUNDS_BINARY;
+    opt->leaves = 4096;
+    opt->train_steps = 300;
+    opt->train_samples = 65536;
+    opt->learning_rate = 0.02f;
+    opt->chunk = 0;
+    opt->mask_budget_mb = 4096;
+    opt->reorder_queries = 1;
+}
+
+sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
+                     const sfc_options* opt, void* stream)
+{
+    if (!out) return SFC_ERR_INVALID;
+    *out = nullptr;
+    if (n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
+    if (curve != SFC_CURVE_Z && curve != SFC_CURVE_HILBERT) return SFC_ERR_INVALID;
+    sfc_options o;
+    sfc_default_options(&o);
+    if (opt) o = *opt;
+    if (o.leaves < 1 || o.leaves > (1 << 20) || o.mask_budget_mb < 1 || o.train_samples < 2 ||
+        o.train_steps < 0 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
+        (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED))
+        return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    sfc_index* idx = new (std::nothrow) sfc_index();
+    if (!idx) return SFC_ERR_OOM;
+    cudaGetDevice(&idx->device);
+    idx->curve = curve;
+    idx->n = n;
+    idx->opt = o;
+    idx->bounds = SFC_BOUNDS_BINARY;
+    idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;
+    idx->last_stream = st;
+    sfc_status s = ensure_status_buf(idx, st);
+    if (s == SFC_OK) s = build_from_device(idx, d_points, st);
+    if (s == SFC_OK && o.bounds == SFC_BOUNDS_LEARNED) {
+        s = train_model(idx, st);
+        if (s == SFC_OK) idx->bounds = SFC_BOUNDS_LEARNED;
+    }
+    if (s != SFC_OK) {
+        sfc_destroy(idx);
+        return s;
+    }
+    *out = idx;
+    return SFC_OK;
+}
+
+sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, sfc_curve curve,
+                          const sfc_options* opt, void* stream)
+{
+    if (!out) return SFC_ERR_INVALID;
+    *out = nullptr;
+    if (n >= 0xffffffffull || (n && !h_points)) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    void* d = nullptr;
+    SFC_TRY(dev_alloc(&d, n * sizeof(int2), st));
+    cudaError_t e = n ? cudaMemcpyAsync(d, h_points, n * sizeof(int2), cudaMemcpyHostToDevice, st) : cudaSuccess;
+    sfc_status s = e == cudaSuccess ? sfc_build(out, static_cast<int32_t*>(d), n, curve, opt, stream) : SFC_ERR_CUDA;
+    dev_free(d, st);
+    return s;
+}
+
+void sfc_destroy(sfc_index* idx)
+{
+    if (!idx) return;
+    cudaStream_t st = idx->last_stream;
+    release_index(idx, st);
+    delete idx;
+}
+
+sfc_status sfc_query_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                           uint64_t* d_out_offsets, void* stream)
+{
+    if (!idx || !d_out_offsets || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
+    idx->last_stream = as_stream(stream);
+    return do_count(idx, d_q, d_delta, m, d_out_offsets, as_stream(stream));
+}
+
+sfc_status sfc_query_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                           const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t ids_capacity,
+                           void* stream)
+{
+    if (!idx || !d_out_offsets || (ids_capacity && !d_out_ids)) return SFC_ERR_INVALID;
+    idx->last_stream = as_stream(stream);
+    return do_write(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, ids_capacity, as_stream(stream));
+}
+
+sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                           uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t ids_capacity,
+                           void* stream)
+{
+    SFC_TRY(sfc_query_count(idx, d_q, d_delta, m, d_out_offsets, stream));
+    return sfc_query_write(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, ids_capacity, stream);
+}
+
+sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta, uint64_t m,
+                                uint64_t* h_out_offsets, uint32_t* h_out_ids, uint64_t ids_capacity,
+                                void* stream)
+{
+    if (!idx || !h_out_offsets || (m && (!h_q || !h_delta)) || (ids_capacity && !h_out_ids) ||
+        m >= 0xffffffffull)
+        return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    idx->last_stream = st;
+    HostStage& hs = idx->stage;
+    SFC_TRY(hs.q.ensure(m * sizeof(int2), st));
+    SFC_TRY(hs.delta.ensure(m * sizeof(int32_t), st));
+    SFC_TRY(hs.offsets.ensure((m + 1) * sizeof(uint64_t), st));
+    int32_t* dq = hs.q.as<int32_t>();
+    int32_t* dd = hs.delta.as<int32_t>();
+    uint64_t* doff = hs.offsets.as<uint64_t>();
+    if (m) {
+        SFC_CUDA_TRY(cudaMemcpyAsync(dq, h_q, m * sizeof(int2), cudaMemcpyHostToDevice, st));
+        SFC_CUDA_TRY(cudaMemcpyAsync(dd, h_delta, m * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    SFC_TRY(do_count(idx, dq, dd, m, doff, st));
+    SFC_CUDA_TRY(cudaMemcpyAsync(h_out_offsets, doff, (m + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint64_t total = h_out_offsets[m];
+    if (total > ids_capacity) {
+        idx->qws.pending.valid = false;
+        return SFC_ERR_CAPACITY;
+    }
+    SFC_TRY(hs.ids.ensure(total * sizeof(uint32_t), st));
+    SFC_TRY(do_write(idx, dq, dd, m, doff, hs.ids.as<uint32_t>(), total, st));
+    if (total)
+        SFC_CUDA_TRY(cudaMemcpyAsync(h_out_ids, hs.ids.ptr, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    return SFC_OK;
+}
+
+sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream)
+{
+    if (!idx) return SFC_ERR_INVALID;
+    SFC_TRY(ensure_status_buf(idx, as_stream(stream)));
+    return ensure_query_ws(idx, m, as_stream(stream));
+}
+
+sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode)
+{
+    if (!idx || (mode != SFC_BOUNDS_BINARY && mode != SFC_BOUNDS_LEARNED)) return SFC_ERR_INVALID;
+    if (mode == SFC_BOUNDS_LEARNED && !idx->model.trained) return SFC_ERR_STATE;
+    idx->bounds = mode;
+    return SFC_OK;
+}
+
+sfc_status sfc_train_model(sfc_index* idx, void* stream)
+{
+    if (!idx) return SFC_ERR_INVALID;
+    idx->last_stream = as_stream(stream);
+    return train_model(idx, as_stream(stream));
+}
+
+sfc_status sfc_model_stats(const sfc_index* cidx, uint64_t* h_endpoints, uint64_t* h_misses,
+                           uint64_t* h_window_sum, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx) return SFC_ERR_INVALID;
+    unsigned long long v[3];
+    cudaStream_t st = as_stream(stream);
+    SFC_CUDA_TRY(cudaMemcpyAsync(v, model_stats(idx), sizeof(v), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_endpoints) *h_endpoints = v[0];
+    if (h_misses) *h_misses = v[1];
+    if (h_window_sum) *h_window_sum = v[2];
+    return SFC_OK;
+}
+
+sfc_status sfc_get_sorted(const sfc_index* idx, const uint64_t** d_keys, const uint32_t** d_ids,
+                          const int32_t** d_xy, uint64_t* n)
+{
+    if (!idx) return SFC_ERR_INVALID;
+    if (d_keys) *d_keys = idx->keys.as<uint64_t>();
+    if (d_ids) *d_ids = idx->ids.as<uint32_t>();
+    if (d_xy) *d_xy = idx->xy.as<int32_t>();
+    if (n) *n = idx->n;
+    return SFC_OK;
+}
+
+sfc_status sfc_device_status(sfc_index* idx, uint32_t* h_bits, void* stream)
+{
+    if (!idx) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    SFC_TRY(ensure_status_buf(idx, st));
+    uint32_t bits = 0;
+    SFC_CUDA_TRY(cudaMemcpyAsync(&bits, idx->status.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaMemsetAsync(idx->status.ptr, 0, sizeof(uint32_t), st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_bits) *h_bits = bits;
+    if (bits & SFC_DEV_TIMEOUT) return SFC_ERR_TIMEOUT;
+    if (bits & (SFC_DEV_BAD_POINT | SFC_DEV_BAD_QUERY)) return SFC_ERR_INVALID;
+    if (bits & SFC_DEV_NOT_FOUND) return SFC_ERR_NOT_FOUND;
+    if (bits & SFC_DEV_CAPACITY) return SFC_ERR_CAPACITY;
+    return SFC_OK;
+}
+
+sfc_status sfc_keys(const int32_t* d_points, uint64_t n, sfc_curve curve, uint64_t* d_keys, void* stream)
+{
+    if ((n && (!d_points || !d_keys)) || (curve != SFC_CURVE_Z && curve != SFC_CURVE_HILBERT))
+        return SFC_ERR_INVALID;
+    return launch_keys(reinterpret_cast<const int2*>(d_points), n, curve, d_keys, nullptr, as_stream(stream));
+}
+
+sfc_status sfc_decode(const uint64_t* d_keys, uint64_t n, sfc_curve curve, int32_t* d_points, void* stream)
+{
+    if ((n && (!d_points || !d_keys)) || (curve != SFC_CURVE_Z && curve != SFC_CURVE_HILBERT))
+        return SFC_ERR_INVALID;
+    return launch_decode(d_keys, n, curve, reinterpret_cast<int2*>(d_points), as_stream(stream));
+}
+
+sfc_status sfc_sort_pairs(const uint64_t* d_keys_in, const uint32_t* d_ids_in, uint64_t n,
+                          uint64_t* d_keys_out, uint32_t* d_ids_out, void* stream)
+{
+    if (n >= 0xffffffffull || (n && (!d_keys_in || !d_keys_out || !d_ids_out))) return SFC_ERR_INVALID;
+    if (n == 0) return SFC_OK;
+    cudaStream_t st = as_stream(stream);
+    SortWorkspace ws;
+    SortSource src;
+    src.keys = d_keys_in;
+    src.vals = d_ids_in;
+    SortDest dst;
+    dst.keys = d_keys_out;
+    dst.vals = d_ids_out;
+    sfc_status s = radix_sort(src, n, dst, ws, nullptr, st);
+    release_sort_ws(ws, st);
+    return s;
+}
+
+sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream)
+{
+    if (!d_out || (n && !d_in)) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    ScanWorkspace ws;
+    sfc_status s = exclusive_scan_u32(d_in, n, d_out, ws, nullptr, st);
+    ws.flags.release(st);
+    return s;
+}
+
+sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                            uint64_t* d_lo, uint64_t* d_hi, uint32_t* d_begin, uint32_t* d_end,
+                            uint32_t* d_count, void* stream)
+{
+    if (!idx || (m && (!d_q || !d_delta))) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    SFC_TRY(ensure_status_buf(idx, st));
+    QueryArgs a = base_args(idx, d_q, d_delta, m);
+    LearnedModelView lv;
+    return launch_ranges(a, model_view(idx, lv), d_lo, d_hi, d_begin, d_end, d_count, st);
+}
+
+uint64_t sfc_launch_count(void) { return g_launches.load(); }
+
+const char* sfc_status_string(sfc_status s)
+{
+    switch (s) {
+        case SFC_OK: return "SFC_OK";
+        case SFC_ERR_INVALID: return "SFC_ERR_INVALID";
+        case SFC_ERR_OOM: return "SFC_ERR_OOM";
+        case SFC_ERR_CAPACITY: return "SFC_ERR_CAPACITY";
+        case SFC_ERR_NOT_FOUND: return "SFC_ERR_NOT_FOUND";
+        case SFC_ERR_TIMEOUT: return "SFC_ERR_TIMEOUT";
+        case SFC_ERR_CUDA: return "SFC_ERR_CUDA";
+        case SFC_ERR_STATE: return "SFC_ERR_STATE";
+    }
+    return "SFC_ERR_UNKNOWN";
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// The opaque index object behind the C ABI and the host functions that operate on it.
+#pragma once
+
+#include "sfc_internal.cuh"
+
+namespace sfc {
+
+struct PendingCount {       // plan kept between sfc_query_count and sfc_query_write
+    bool valid;
+    const int32_t* q;
+    const int32_t* delta;
+    uint64_t m;
+    const uint64_t* offsets;
+    uint32_t chunk;
+};
+
+struct QueryWs {
+    DevBuf ranges, nchunks, chunk_base, counts, masks, ctr;
+    PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0};
+};
+
+struct HostStage {          // device staging of sfc_query_batch_host
+    DevBuf q, delta, offsets, ids;
+};
+
+struct ModelState {
+    bool trained = false;
+    int nleaves = 0;
+    RootParams root{};                    // derived parameters used by the predict path
+    float theta[3 * kHidden + 1] = {};    // trained (alpha, beta, b, c)
+    DevBuf leaves;                        // LeafParams[nleaves]
+    DevBuf scratch;                       // training samples, gradients, optimiser state
+};
+
+struct UpdateWs {
+    DevBuf a, b, c, d, e, f, g, h;
+};
+
+}  // namespace sfc
+
+struct sfc_index {
+    int device = 0;
+    sfc_curve curve = SFC_CURVE_Z;
+    uint64_t n = 0;                     // live points
+    uint32_t next_id = 0;               // first id not yet issued
+    sfc_options opt{};
+    sfc_bounds bounds = SFC_BOUNDS_BINARY;
+    uint32_t chunk = 1024;              // points per scan chunk
+    uint32_t batch = 4;                 // chunks per work-queue grab
+    uint32_t qbatch = 8;                // queries per write-queue grab
+    cudaStream_t last_stream = nullptr;
+
+    sfc::DevBuf keys, ids, xy;          // the sorted array A_P and its keys
+    sfc::DevBuf xy_by_id;               // coordinates by id (dynamic setting)
+    sfc::DevBuf alive;                  // liveness bitmap by id
+    sfc::DevBuf status;                 // device status word + model statistics
+
+    sfc::SortWorkspace sort_ws;
+    sfc::ScanWorkspace scan_ws;
+    sfc::QueryWs qws;
+    sfc::HostStage stage;
+    sfc::ModelState model;
+    sfc::UpdateWs uws;
+};
+
+namespace sfc {
+
+sfc_status ensure_alive_bits(sfc_index* idx, uint64_t ids, cudaStream_t st);
+void release_index(sfc_index* idx, cudaStream_t st);
+sfc_status train_model(sfc_index* idx, cudaStream_t st);
+
+}  // namespace sfc

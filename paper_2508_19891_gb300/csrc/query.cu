@@ -1,0 +1,535 @@
+// Batched distance query (Alg. 1 for m queries at once).
+//
+//   plan_kernel    one thread per query: bounding square Q of B_delta(q), the level l with
+//                  2 delta <= 2^l < 4 delta, the <= 4 cells of cells(Q) and their key
+//                  intervals [pi(C)o0, pi(C)o1] (Observation), sorted and with abutting
+//                  intervals merged, then lower_bound of both ends of every interval, by
+//                  binary search or by the learned model (verified, with fallback).  The
+//                  query's scan length S_q is cut into chunks of C points.
+//   scan           exclusive scan of the chunk counts -> chunk bases.
+//   count_kernel   persistent warps take batches of chunks from a counter (work stealing);
+//                  a warp streams the chunk's coordinates, applies the exact int64 filter
+//                  dx^2 + dy^2 <= delta^2, keeps the warp ballots as a hit bitmask (one bit
+//                  per scanned point) and adds the chunk's popcount to the query's count.
+//   scan           exclusive scan of the per-query counts -> the caller's out_offsets.
+//   write_kernel   persistent warps take batches of queries; a warp walks its query's
+//                  chunks in order, reads the bitmask (or, past the bitmask budget, re-runs
+//                  the filter) and writes the ids of the hits with ballot/popc compaction at
+//                  out_offsets[q] + rank, so each query's ids come out in array order.
+//
+// The bitmask makes the second pass read 1 bit instead of 8 bytes per scanned point.
+#include "sfc_internal.cuh"
+#include "query.cuh"
+
+namespace sfc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------------------------------
+// Ranges (cells(Q) with merged abutting intervals)
+// ------------------------------------------------------------------------------------
+struct QueryRanges {
+    uint64_t lo[4], hi[4];
+    int cnt;
+};
+
+__device__ __forceinline__ void derive_ranges(int curve, const HilbertTables* tb, int32_t qx,
+                                              int32_t qy, int32_t delta, QueryRanges& R)
+{
+    const int64_t d = delta;
+    const int64_t x0 = max((int64_t)0, (int64_t)qx - d), x1 = min((int64_t)kSide - 1, (int64_t)qx + d);
+    const int64_t y0 = max((int64_t)0, (int64_t)qy - d), y1 = min((int64_t)kSide - 1, (int64_t)qy + d);
+    int l = 0;
+    if (d > 0) {
+        l = 64 - __clzll((unsigned long long)(2 * d - 1));   // bit length of 2 delta - 1
+        if (l > kOmega) l = kOmega;
+    }
+    const uint64_t span = (l >= kOmega) ? kKeyMax : ((1ull << (2 * l)) - 1);
+    int cnt = 0;
+    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
+        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
+            if (cnt == 4) break;   // unreachable: x1 - x0 <= 2 delta <= 2^l gives <= 2 per axis
+            uint64_t k = curve_key(curve, tb, (uint32_t)(cx << l), (uint32_t)(cy << l));
+            uint64_t lo = k & ~span;
+            // insertion in lo order
+            int j = cnt;
+            while (j > 0 && R.lo[j - 1] > lo) { R.lo[j] = R.lo[j - 1]; R.hi[j] = R.hi[j - 1]; --j; }
+            R.lo[j] = lo;
+            R.hi[j] = lo | span;
+            ++cnt;
+        }
+    }
+    // merge intervals that abut in key order (the scan over them is identical)
+    int m = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (m > 0 && R.hi[m - 1] + 1 == R.lo[i]) {
+            R.hi[m - 1] = R.hi[i];
+        } else {
+            R.lo[m] = R.lo[i];
+            R.hi[m] = R.hi[i];
+            ++m;
+        }
+    }
+    R.cnt = m;
+}
+
+__device__ __forceinline__ bool query_valid(int32_t qx, int32_t qy, int32_t delta)
+{
+    return point_in_domain(qx, qy) && delta >= 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Bound search: K lower_bounds in lock step (independent loads in flight together)
+// ------------------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void lower_bounds_window(const uint64_t* __restrict__ keys,
+                                                    const uint64_t* t, uint32_t* lo,
+                                                    uint32_t* len)
+{
+    // answer of search e lies in [lo[e], lo[e] + len[e]]
+    while (true) {
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < K; ++e) any |= len[e] > 0;
+        if (!any) break;
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            if (len[e] > 0) {
+                uint32_t half = len[e] >> 1;
+                uint64_t k = __ldg(keys + lo[e] + half);
+                bool right = k < t[e];
+                lo[e] = right ? lo[e] + half + 1 : lo[e];
+                len[e] = right ? len[e] - half - 1 : half;
+            }
+        }
+    }
+}
+
+struct BinaryBounds {
+    __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
+                                               uint32_t* r, int ne) const
+    {
+        uint32_t lo[8], len[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) { lo[e] = 0; len[e] = e < ne ? n : 0; }
+        lower_bounds_window<8>(keys, t, lo, len);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = lo[e];
+    }
+};
+
+struct LearnedBounds {
+    RootParams root;
+    const LeafParams* leaf;
+    unsigned long long* stats;   // [0] endpoints, [1] misses, [2] window sum
+    __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
+                                               uint32_t* r, int ne) const
+    {
+        uint32_t lo[8], len[8];
+        unsigned long long wsum = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            lo[e] = 0;
+            len[e] = 0;
+            if (e < ne) {
+                const int j = route_leaf(root, t[e]);
+                const LeafParams lp = leaf[j];
+                const int64_t p = leaf_predict(lp, t[e]);
+                int64_t a = p + lp.err_lo, b = p + (int64_t)lp.err_hi + 1;
+                a = max(a, (int64_t)lp.first);
+                a = min(a, (int64_t)lp.end);
+                b = max(b, a);
+                b = min(b, (int64_t)lp.end);
+                lo[e] = (uint32_t)a;
+                len[e] = (uint32_t)(b - a);
+                wsum += len[e];
+            }
+        }
+        lower_bounds_window<8>(keys, t, lo, len);
+        // verify: lower_bound is the unique r with keys[r-1] < t <= keys[r]
+        uint32_t miss = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if (e < ne) {
+                const uint32_t x = lo[e];
+                const bool ok = (x == 0 || __ldg(keys + x - 1) < t[e]) && (x == n || __ldg(keys + x) >= t[e]);
+                if (!ok) { miss |= 1u << e; lo[e] = 0; len[e] = n; }
+            }
+        }
+        if (miss) lower_bounds_window<8>(keys, t, lo, len);   // full binary search fallback
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = lo[e];
+        if (stats) {
+            unsigned long long c = ne, mc = __popc(miss);
+            // one atomic per warp
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+                mc += __shfl_xor_sync(0xffffffffu, mc, o);
+                wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+            }
+            if (lane_id() == 0) {
+                atomicAdd(stats + 0, c);
+                atomicAdd(stats + 1, mc);
+                atomicAdd(stats + 2, wsum);
+            }
+        }
+    }
+};
+
+// Range derivation + bound search for one query; returns the merged intervals' bounds.
+template <class Bounds>
+__device__ __forceinline__ int query_bounds(const Bounds& bounds, int curve, const HilbertTables* tb,
+                                            const uint64_t* keys, uint32_t n, bool ok, int32_t qx,
+                                            int32_t qy, int32_t delta, QueryRanges& R, uint32_t* b,
+                                            uint32_t* e)
+{
+    R.cnt = 0;
+    if (ok) derive_ranges(curve, tb, qx, qy, delta, R);
+    uint64_t t[8];
+    const int ne = 2 * R.cnt;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        t[2 * i] = i < R.cnt ? R.lo[i] : 0;
+        t[2 * i + 1] = i < R.cnt ? R.hi[i] + 1 : 0;
+    }
+    uint32_t r[8];
+    bounds(keys, n, t, r, ne);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        b[i] = i < R.cnt ? r[2 * i] : 0;
+        e[i] = i < R.cnt ? r[2 * i + 1] : 0;
+    }
+    return R.cnt;
+}
+
+// ------------------------------------------------------------------------------------
+// plan_kernel
+// ------------------------------------------------------------------------------------
+template <class Bounds>
+__global__ void __launch_bounds__(kThreads) plan_kernel(QueryArgs a, Bounds bounds)
+{
+    __shared__ HilbertTables tb;
+    if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = i < a.m;
+    int2 q = make_int2(0, 0);
+    int32_t delta = -1;
+    if (active) {
+        q = reinterpret_cast<const int2*>(a.q)[i];
+        delta = a.delta[i];
+    }
+    const bool ok = active && query_valid(q.x, q.y, delta);
+    if (active && !ok) set_status(a.status, SFC_DEV_BAD_QUERY);
+    uint32_t b[4], e[4];
+    QueryRanges R;
+    // every lane calls the bound search (with no endpoints when inactive or invalid), so
+    // warp-collective statistics inside it see a converged warp
+    query_bounds(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, R, b, e);
+    if (!active) return;
+    uint64_t S = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) S += e[k] - b[k];
+    uint4* rp = reinterpret_cast<uint4*>(a.ranges + 8 * i);
+    rp[0] = make_uint4(b[0], e[0], b[1], e[1]);
+    rp[1] = make_uint4(b[2], e[2], b[3], e[3]);
+    a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+}
+
+// ------------------------------------------------------------------------------------
+// Shared helpers of the two scan passes
+// ------------------------------------------------------------------------------------
+struct QView {
+    uint32_t b0, b1, b2, b3;
+    uint32_t c1, c2, c3, S;   // cumulative starts of intervals 1..3 and the total
+    int2 q;
+    int64_t d2;
+};
+
+__device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi)
+{
+    QView v;
+    const uint4* rp = reinterpret_cast<const uint4*>(a.ranges + 8 * qi);
+    uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    v.b0 = r0.x; v.b1 = r0.z; v.b2 = r1.x; v.b3 = r1.z;
+    v.c1 = r0.y - r0.x;
+    v.c2 = v.c1 + (r0.w - r0.z);
+    v.c3 = v.c2 + (r1.y - r1.x);
+    v.S = v.c3 + (r1.w - r1.z);
+    v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
+    const int64_t d = __ldg(a.delta + qi);
+    v.d2 = d * d;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t map_pos(const QView& v, uint32_t f)
+{
+    return f < v.c1 ? v.b0 + f : f < v.c2 ? v.b1 + (f - v.c1) : f < v.c3 ? v.b2 + (f - v.c2) : v.b3 + (f - v.c3);
+}
+
+__device__ __forceinline__ bool is_hit(const QView& v, int2 p)
+{
+    const int64_t dx = (int64_t)p.x - v.q.x, dy = (int64_t)p.y - v.q.y;
+    return dx * dx + dy * dy <= v.d2;
+}
+
+// Filters points [s0, s1) of the query's concatenated intervals; returns the hit count and
+// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.
+template <int WPL>
+__device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, uint32_t s0,
+                                                 uint32_t s1, uint32_t (&words)[WPL])
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) words[s] = 0;
+    uint32_t cnt = 0;
+    const uint32_t nit = (s1 - s0 + 31) >> 5;
+    const int2* __restrict__ xy = a.xy;
+    for (uint32_t it = 0; it < nit; it += 4) {
+        int2 p[4];
+        bool val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t f = s0 + ((it + u) << 5) + lane;
+            val[u] = f < s1;
+            p[u] = val[u] ? __ldcs(xy + map_pos(v, f)) : make_int2(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t w = __ballot_sync(0xffffffffu, val[u] && is_hit(v, p[u]));
+            cnt += __popc(w);
+            const uint32_t wi = it + u;
+#pragma unroll
+            for (int s = 0; s < WPL; ++s)
+                if (wi == (uint32_t)(s * 32) + lane) words[s] = w;
+        }
+    }
+    return cnt;
+}
+
+// Warp-cooperative search: the query owning chunk g (largest q with base[q] <= g).
+__device__ __forceinline__ uint64_t owner_query(const uint64_t* __restrict__ base, uint64_t m, uint64_t g)
+{
+    uint64_t lo = 0, hi = m;   // base[lo] <= g < base[hi]
+    const unsigned lane = lane_id();
+    while (hi - lo > 1) {
+        const uint64_t step = (hi - lo + 31) >> 5;
+        const uint64_t pos = lo + lane * step;
+        const bool le = pos < hi && __ldg(base + pos) <= g;
+        const uint32_t bal = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(bal);
+        const uint64_t nlo = lo + (uint64_t)last * step;
+        const uint64_t nhi = min(hi, nlo + step);
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------------------
+// count_kernel
+// ------------------------------------------------------------------------------------
+template <int WPL>
+__global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
+{
+    const unsigned lane = lane_id();
+    const uint64_t G = a.chunk_base[a.m];
+    const uint32_t W = a.chunk >> 5;   // mask words per chunk
+    while (true) {
+        uint64_t g0 = 0;
+        if (lane == 0) g0 = atomicAdd(a.work_ctr, (unsigned long long)a.batch);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        if (g0 >= G) break;
+        const uint64_t g1 = min(G, g0 + a.batch);
+        uint64_t q = owner_query(a.chunk_base, a.m, g0);
+        for (uint64_t g = g0; g < g1; ++g) {
+            while (__ldg(a.chunk_base + q + 1) <= g) ++q;
+            const QView v = load_query(a, q);
+            const uint32_t j = (uint32_t)(g - __ldg(a.chunk_base + q));
+            const uint32_t s0 = j * a.chunk;
+            const uint32_t s1 = min(v.S, s0 + a.chunk);
+            uint32_t words[WPL];
+            const uint32_t cnt = filter_chunk<WPL>(a, v, s0, s1, words);
+            if (g < a.mask_chunks) {
+                const uint32_t nw = (s1 - s0 + 31) >> 5;
+                uint32_t* mp = a.masks + g * W;
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) {
+                    const uint32_t wi = s * 32 + lane;
+                    if (wi < nw) mp[wi] = words[s];
+                }
+            }
+            if (lane == 0 && cnt) atomicAdd(a.counts + q, cnt);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// write_kernel
+// ------------------------------------------------------------------------------------
+template <int WPL>
+__global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
+{
+    const unsigned lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
+        set_status(a.status, SFC_DEV_CAPACITY);
+    const uint32_t W = a.chunk >> 5;
+    while (true) {
+        uint64_t q0 = 0;
+        if (lane == 0) q0 = atomicAdd(a.work_ctr + 1, (unsigned long long)a.qbatch);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= a.m) break;
+        const uint64_t q1 = min(a.m, q0 + a.qbatch);
+        for (uint64_t q = q0; q < q1; ++q) {
+            const uint32_t k = __ldg(a.counts + q);
+            if (k == 0) continue;
+            const QView v = load_query(a, q);
+            const uint64_t off = a.out_offsets[q];
+            const uint64_t cb = __ldg(a.chunk_base + q);
+            const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
+            uint32_t rank = 0;
+            for (uint64_t j = 0; j < nch && rank < k; ++j) {
+                const uint64_t g = cb + j;
+                const uint32_t s0 = (uint32_t)j * a.chunk;
+                const uint32_t s1 = min(v.S, s0 + a.chunk);
+                const uint32_t nw = (s1 - s0 + 31) >> 5;
+                uint32_t words[WPL];
+                if (g < a.mask_chunks) {
+                    const uint32_t* mp = a.masks + g * W;
+#pragma unroll
+                    for (int s = 0; s < WPL; ++s) {
+                        const uint32_t wi = s * 32 + lane;
+                        words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
+                    }
+                } else {
+                    filter_chunk<WPL>(a, v, s0, s1, words);
+                }
+                for (uint32_t wi = 0; wi < nw; ++wi) {
+                    uint32_t mine = words[0];
+#pragma unroll
+                    for (int s = 1; s < WPL; ++s)
+                        if ((wi >> 5) == (uint32_t)s) mine = words[s];
+                    const uint32_t w = __shfl_sync(0xffffffffu, mine, wi & 31);
+                    if (w == 0) continue;
+                    if ((w >> lane) & 1u) {
+                        const uint32_t pos = map_pos(v, s0 + (wi << 5) + lane);
+                        const uint64_t dst = off + rank + __popc(w & lt);
+                        if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
+                    }
+                    rank += __popc(w);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// ranges export (tests)
+// ------------------------------------------------------------------------------------
+template <class Bounds>
+__global__ void __launch_bounds__(kThreads) ranges_kernel(QueryArgs a, Bounds bounds, uint64_t* out_lo,
+                                                          uint64_t* out_hi, uint32_t* out_b,
+                                                          uint32_t* out_e, uint32_t* out_cnt)
+{
+    __shared__ HilbertTables tb;
+    if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = i < a.m;
+    int2 q = make_int2(0, 0);
+    int32_t delta = -1;
+    if (active) {
+        q = reinterpret_cast<const int2*>(a.q)[i];
+        delta = a.delta[i];
+    }
+    const bool ok = active && query_valid(q.x, q.y, delta);
+    QueryRanges R;
+    uint32_t b[4], e[4];
+    query_bounds(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, R, b, e);
+    if (!active) return;
+    for (int k = 0; k < 4; ++k) {
+        const bool u = k < R.cnt;
+        if (out_lo) out_lo[4 * i + k] = u ? R.lo[k] : 1;
+        if (out_hi) out_hi[4 * i + k] = u ? R.hi[k] : 0;
+        if (out_b) out_b[4 * i + k] = b[k];
+        if (out_e) out_e[4 * i + k] = e[k];
+    }
+    if (out_cnt) out_cnt[i] = (uint32_t)R.cnt;
+}
+
+int persistent_grid(const void* fn)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm * num_sms();
+}
+
+template <int WPL>
+sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
+{
+    if (!write) {
+        int g = persistent_grid((const void*)count_kernel<WPL>);
+        count_kernel<WPL><<<g, kThreads, 0, st>>>(a);
+    } else {
+        int g = persistent_grid((const void*)write_kernel<WPL>);
+        write_kernel<WPL><<<g, kThreads, 0, st>>>(a);
+    }
+    count_launch();
+    return launch_status();
+}
+
+}  // namespace
+
+sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st)
+{
+    if (a.m == 0) return SFC_OK;
+    const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
+    if (lm) {
+        LearnedBounds lb{lm->root, lm->leaf, lm->stats};
+        plan_kernel<LearnedBounds><<<g, kThreads, 0, st>>>(a, lb);
+    } else {
+        plan_kernel<BinaryBounds><<<g, kThreads, 0, st>>>(a, BinaryBounds{});
+    }
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_count(const QueryArgs& a, cudaStream_t st)
+{
+    if (a.m == 0) return SFC_OK;
+    switch (a.chunk >> 10) {
+        case 0: case 1: return launch_count_write<1>(a, false, st);
+        case 2: return launch_count_write<2>(a, false, st);
+        default: return launch_count_write<4>(a, false, st);
+    }
+}
+
+sfc_status launch_write(const QueryArgs& a, cudaStream_t st)
+{
+    if (a.m == 0) return SFC_OK;
+    switch (a.chunk >> 10) {
+        case 0: case 1: return launch_count_write<1>(a, true, st);
+        case 2: return launch_count_write<2>(a, true, st);
+        default: return launch_count_write<4>(a, true, st);
+    }
+}
+
+sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_t* lo, uint64_t* hi,
+                         uint32_t* b, uint32_t* e, uint32_t* cnt, cudaStream_t st)
+{
+    if (a.m == 0) return SFC_OK;
+    const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
+    if (lm) {
+        LearnedBounds lb{lm->root, lm->leaf, lm->stats};
+        ranges_kernel<LearnedBounds><<<g, kThreads, 0, st>>>(a, lb, lo, hi, b, e, cnt);
+    } else {
+        ranges_kernel<BinaryBounds><<<g, kThreads, 0, st>>>(a, BinaryBounds{}, lo, hi, b, e, cnt);
+    }
+    count_launch();
+    return launch_status();
+}
+
+}  // namespace sfc

@@ -1,0 +1,45 @@
+// Arguments and launchers of the query pipeline (query.cu), shared with the C-ABI layer.
+#pragma once
+
+#include "sfc_internal.cuh"
+
+namespace sfc {
+
+struct QueryArgs {
+    int curve;
+    const uint64_t* keys;        // sorted keys [n]
+    const uint32_t* ids;         // ids in sorted order [n]
+    const int2* xy;              // coordinates in sorted order [n]
+    uint32_t n;
+    const int32_t* q;            // [m][2]
+    const int32_t* delta;        // [m]
+    uint64_t m;
+    uint32_t* ranges;            // [m][8]: (begin, end) of up to four intervals
+    uint32_t* nchunks;           // [m]
+    uint64_t* chunk_base;        // [m + 1]
+    uint32_t* counts;            // [m] hits per query
+    uint32_t* masks;             // hit bitmask, chunk g at masks + g * (chunk / 32)
+    uint64_t mask_chunks;        // chunks that fit in the bitmask buffer
+    uint32_t chunk;              // points per chunk (multiple of 32, <= 4096)
+    uint32_t batch;              // chunks taken per work-queue grab (count pass)
+    uint32_t qbatch;             // queries taken per grab (write pass)
+    unsigned long long* work_ctr;  // [0] count-pass queue, [1] write-pass queue
+    uint64_t* out_offsets;       // [m + 1]
+    uint32_t* out_ids;
+    uint64_t ids_capacity;
+    uint32_t* status;
+};
+
+struct LearnedModelView {
+    RootParams root;
+    const LeafParams* leaf;
+    unsigned long long* stats;   // [3]: endpoints, misses, window sum
+};
+
+sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st);
+sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
+sfc_status launch_write(const QueryArgs& a, cudaStream_t st);
+sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_t* lo, uint64_t* hi,
+                         uint32_t* b, uint32_t* e, uint32_t* cnt, cudaStream_t st);
+
+}  // namespace sfc

@@ -1,0 +1,147 @@
+// Exclusive prefix sum uint32[n] -> uint64[n + 1] in one pass over the data: single-pass
+// scan with decoupled look-back (Merrill & Garland, 2016).  Used to turn per-query chunk
+// counts into chunk bases and per-query hit counts into output offsets.
+//
+// Each block takes the next tile index from a counter (so a tile's predecessors are
+// already running and will publish), reduces its tile, publishes the aggregate, reads the
+// predecessors' words a warp at a time until it meets an inclusive prefix, then publishes
+// its own inclusive prefix and writes its outputs.  A word packs a 2-bit flag with a
+// 62-bit sum.  The wait on a predecessor is bounded: past kSpinLimit reads it sets
+// SFC_DEV_TIMEOUT and continues with the partial sum.
+#include "sfc_internal.cuh"
+
+namespace sfc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+scan_kernel(const uint32_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ out,
+            uint64_t* flags /* [0] = tile counter, [1 + t] = tile words */, uint32_t* status,
+            int vec)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_warp[kThreads / 32];
+    __shared__ uint64_t s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(reinterpret_cast<unsigned long long*>(flags), 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t base = tile * kTile + (uint64_t)tid * kItems;
+
+    uint32_t v[kItems];
+    if (vec && base + kItems <= n) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + base);
+#pragma unroll
+        for (int j = 0; j < kItems / 4; ++j) {
+            uint4 u = __ldcs(p + j);
+            v[4 * j] = u.x; v[4 * j + 1] = u.y; v[4 * j + 2] = u.z; v[4 * j + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) v[j] = (base + j < n) ? in[base + j] : 0u;
+    }
+    uint64_t tsum = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) tsum += v[j];
+
+    uint64_t incl = warp_incl_scan(tsum);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < kThreads / 32 ? s_warp[lane] : 0;
+        uint64_t wi = warp_incl_scan(w);
+        if (lane < kThreads / 32) s_warp[lane] = wi - w;   // exclusive warp offsets
+        uint64_t total = __shfl_sync(0xffffffffu, wi, 31);
+        // ---- decoupled look-back ----
+        uint64_t* words = flags + 1;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            if (lane == 0) atomicExch(reinterpret_cast<unsigned long long*>(words), kFlagPrefix | total);
+        } else {
+            if (lane == 0) atomicExch(reinterpret_cast<unsigned long long*>(words + tile), kFlagAgg | total);
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                int64_t idx = t - lane;
+                uint64_t wv = kFlagPrefix;   // lanes before tile 0 act as a zero prefix
+                if (idx >= 0) wv = *reinterpret_cast<volatile uint64_t*>(words + idx);
+                uint32_t notready = __ballot_sync(0xffffffffu, (wv >> 62) == 0);
+                if (notready) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) set_status(status, SFC_DEV_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                uint32_t pref = __ballot_sync(0xffffffffu, (wv >> 62) == 2);
+                uint64_t val = (idx >= 0) ? (wv & kValueMask) : 0;
+                if (pref) {
+                    int first = __ffs(pref) - 1;          // nearest predecessor with a prefix
+                    if (lane > first) val = 0;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                excl += val;
+                if (pref) break;
+                t -= 32;
+            }
+            if (lane == 0)
+                atomicExch(reinterpret_cast<unsigned long long*>(words + tile), kFlagPrefix | (excl + total));
+        }
+        if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    uint64_t run = s_excl + s_warp[warp] + (incl - tsum);
+    uint64_t o[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) { o[j] = run; run += v[j]; }
+    if (vec && base + kItems <= n) {
+        ulonglong2* q = reinterpret_cast<ulonglong2*>(out + base);
+#pragma unroll
+        for (int j = 0; j < kItems / 2; ++j) q[j] = make_ulonglong2(o[2 * j], o[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            if (base + j < n) out[base + j] = o[j];
+    }
+    // the thread holding element n - 1 also writes the total
+    if (base < n && base + kItems >= n) out[n] = run;
+}
+
+}  // namespace
+
+sfc_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, ScanWorkspace& ws,
+                              uint32_t* status, cudaStream_t st)
+{
+    if (n == 0) {
+        SFC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+        return SFC_OK;
+    }
+    uint64_t tiles = (n + kTile - 1) / kTile;
+    if (tiles > 0x7fffffffull) return SFC_ERR_INVALID;
+    SFC_TRY(ws.flags.ensure((tiles + 1) * sizeof(uint64_t), st));
+    SFC_CUDA_TRY(cudaMemsetAsync(ws.flags.ptr, 0, (tiles + 1) * sizeof(uint64_t), st));
+    int vec = ((((uintptr_t)in) & 15) == 0) && ((((uintptr_t)out) & 15) == 0);
+    scan_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(in, n, out, ws.flags.as<uint64_t>(), status, vec);
+    count_launch();
+    return launch_status();
+}
+
+}  // namespace sfc

@@ -30,3 +30,28 @@ def load_grid(name):
         for x, v in enumerate(vals):
             out[(x, y)] = v
     return out
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_19891_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda", 0)
+
+
+def to_dev(a, dev):
+    import torch
+    return torch.from_numpy(a).to(dev)
+
+
+def u32(t):
+    """int32 tensor holding uint32 ids -> numpy uint32."""
+    return t.cpu().numpy().view("uint32")
+
+
+def u64(t):
+    return t.cpu().numpy().view("uint64")
