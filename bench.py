@@ -1,0 +1,446 @@
+"""Benchmark of the batched distance-reporting hot path on GB300.
+
+One step = the whole path over one batch of the mixed-1e7 workload (n = 10^7 points, half
+uniform and half in 1,000 Gaussian clusters; m = 10^6 queries at data points with
+log-uniform expected counts in [1, 2000]): build the Z-order index from points resident in
+HBM (keys + onesweep sort + decode), fit the learned bounds when they are enabled, then
+answer the m queries (ranges, bounds, count, scan, write).  value = queries answered per
+second of step time.  After the timed steps the same run measures, outside the headline:
+the learned-vs-binary query phase, the Hilbert curve, and reports per-step times.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank answers its own independent problem instance (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "queries/s & reported pts/s (learned vs binary search), build pts/s, %HBM peak"
+UNIT = "queries/s"
+WORKLOAD = "mixed-1e7"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
+    ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def instance_seed(rank: int) -> int:
+    """Each rank answers its own instance; rank 0 is the canonical seed of the workload."""
+    return 2 + 7919 * rank
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2508_19891_gb300 as sfc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    wl = workloads.mixed_1e7(scale=args.scale, seed=instance_seed(rank))
+    n, m = wl.n, wl.m
+    bounds = args.bounds or ("learned" if learned_available(sfc) else "binary")
+    pts = torch.from_numpy(wl.points).to(dev)
+    q = torch.from_numpy(wl.queries).to(dev)
+    d = torch.from_numpy(wl.delta).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    opts = dict(bounds=bounds, profile=1)
+
+    # size the output once: the total is the same for every step
+    idx = sfc.sfc_build(pts, "z", **opts)
+    off, ids = sfc.query(idx, q, d)
+    total = int(off[-1].item())
+    idx.close()
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+
+    last = {}
+
+    def step():
+        ix = sfc.sfc_build(pts, "z", **opts)
+        sfc.sfc_query_batch(ix, q, d, off, ids, capacity=total)
+        last["idx"] = ix
+        return ix
+
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = sfc.sfc_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    profs = []
+    for i in range(args.steps):
+        flush.fill_(i & 255)                      # evict L2 between timed steps
+        ev[i][0].record()
+        ix = step()
+        ev[i][1].record()
+        profs.append(ix)
+    torch.cuda.synchronize()
+    launches = sfc.sfc_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pg.barrier()
+    else:
+        total_ms = local_ms
+    # per-step device times of the library's steps (events on the launching stream)
+    agg = {}
+    for ix in profs:
+        for name, (cnt, ms) in sfc.sfc_profile_read(ix, reset=True).items():
+            c0, m0 = agg.get(name, (0, 0.0))
+            agg[name] = (c0 + cnt, m0 + ms)
+    stats = sfc.sfc_query_stats(profs[-1])
+    status, bits = sfc.sfc_device_status(profs[-1])
+    for ix in profs:
+        ix.close()
+    if status != 0:
+        raise RuntimeError(f"device status {status} bits {bits:#x}")
+
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step / 1e3)
+    hbm_peak, peak_kind = peaks()
+    # dominant kernel: the count pass (one launch per step)
+    count_runs, count_ms = agg.get("count", (0, float("nan")))
+    count_avg_ms = count_ms / max(count_runs, 1)
+    S = stats["scanned"]
+    alg_bytes = 8 * S + S // 8          # coordinates read + one mask bit per scanned point
+    achieved = alg_bytes / (count_avg_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "curve": "z", "bounds": bounds,
+                   "seed": instance_seed(rank), "l2": "flushed between timed steps (256 MB write)",
+                   "step": "build (keys+sort+decode) + learned-model fit if enabled + query batch"},
+        "roofline": {"kernel": "count_kernel", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": committed_traffic("count_kernel", alg_bytes),
+                     "algorithmic_bytes": alg_bytes, "avg_launch_ms": count_avg_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "breakdown": {
+            "step_ms": step_ms,
+            "phase_ms_per_step": {k: v[1] / args.steps for k, v in agg.items()},
+            "build_pts_per_s": n / (agg.get("sort", (1, float("nan")))[1] / args.steps / 1e3),
+            "reported_pts_per_s": world * stats["hits"] / (ms_per_step / 1e3),
+            "hits_per_step": stats["hits"], "scanned_per_step": S, "chunks": stats["chunks"],
+            "scan_amplification": S / max(stats["hits"], 1),
+        },
+    }
+    if rank == 0 and not args.no_extras:
+        out["breakdown"].update(extras(sfc, torch, pts, q, d, total, n, m, flush))
+        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args)
+    elif rank == 0:
+        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def learned_available(sfc) -> bool:
+    try:
+        import torch
+        p = torch.zeros((64, 2), dtype=torch.int32, device="cuda")
+        p[:, 0] = torch.arange(64, device="cuda")
+        ix = sfc.sfc_build(p, "z", bounds="learned")
+        ix.close()
+        return True
+    except Exception:
+        return False
+
+
+def committed_traffic(kernel: str, alg_bytes: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        src = os.path.join(ROOT, "paper_2508_19891_gb300", "csrc", e["source"])
+        import hashlib
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != e["source_sha"]:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def timed(fn, torch, flush, reps=3):
+    best = float("inf")
+    for i in range(reps):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def extras(sfc, torch, pts, q, d, total, n, m, flush):
+    """Untimed-for-the-headline measurements: query phase with binary vs learned bounds,
+    Hilbert build and query, and the learned model's window statistics."""
+    out = {}
+    off = torch.empty(m + 1, dtype=torch.int64, device=pts.device)
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device=pts.device)
+    for curve in ("z", "h"):
+        build_ms = timed(lambda: sfc.sfc_build(pts, curve).close(), torch, flush)
+        ix = sfc.sfc_build(pts, curve)
+        res = {"build_ms": build_ms, "build_pts_per_s": n / (build_ms / 1e3)}
+        modes = ["binary"]
+        try:
+            sfc.sfc_train_model(ix)
+            modes.append("learned")
+            tr = timed(lambda: sfc.sfc_train_model(ix), torch, flush)
+            res["train_ms"] = tr
+        except Exception:
+            pass
+        ref_ids = None
+        for mode in modes:
+            sfc.sfc_set_bounds_mode(ix, mode)
+            qms = timed(lambda: sfc.sfc_query_batch(ix, q, d, off, ids, capacity=total), torch, flush)
+            res[f"query_ms_{mode}"] = qms
+            res[f"queries_per_s_{mode}"] = m / (qms / 1e3)
+            res[f"reported_pts_per_s_{mode}"] = total / (qms / 1e3)
+            cur = ids.clone()
+            if ref_ids is None:
+                ref_ids = cur
+            else:
+                res["learned_equals_binary"] = bool(torch.equal(cur, ref_ids))
+            if mode == "learned":
+                res["learned_stats"] = sfc.sfc_model_stats(ix)
+        st = sfc.sfc_device_status(ix)
+        res["device_status"] = st[0]
+        ix.close()
+        out[curve] = res
+    return out
+
+
+def e2e(sfc, torch, wl, total, bounds, args):
+    """The same step through the C ABI with host buffers: sfc_build_host + (model fit) +
+    sfc_query_batch_host, host->device and device->host copies inside the timed region,
+    inputs in pinned host memory."""
+    n, m = wl.n, wl.m
+    hp = torch.empty((n, 2), dtype=torch.int32, pin_memory=True).numpy()
+    hp[:] = wl.points
+    hq = torch.empty((m, 2), dtype=torch.int32, pin_memory=True).numpy()
+    hq[:] = wl.queries
+    hd = torch.empty(m, dtype=torch.int32, pin_memory=True).numpy()
+    hd[:] = wl.delta
+    hoff = torch.empty(m + 1, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hids = torch.empty(max(total, 1), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = sfc.sfc_build_host(hp, "z", bounds=bounds)
+        sfc.sfc_query_batch_host(ix, hq, hd, total, out_offsets=hoff, out_ids=hids)
+        ix.close()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    return {"value": m / t, "unit": UNIT, "h2d_bytes_per_step": n * 8 + m * 12,
+            "d2h_bytes_per_step": (m + 1) * 8 + int(hoff[m]) * 4, "ms_per_step": t * 1e3}
+
+
+# --------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------------------
+
+def oracle_sample(wl, budget_s: float, threads: int):
+    """Oracle build on the whole point set, then as many queries as fit in the remaining
+    budget (at least 1000); returns (queries/s for the whole workload, details)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    idx = oracle.build(wl.points, 30, "z")
+    tb = time.perf_counter() - t0
+    left = max(budget_s - tb, 1.0)
+    k = 2000
+    done = 0
+    tq = 0.0
+    while True:
+        k = min(k, wl.m - done)
+        if k <= 0:
+            break
+        t1 = time.perf_counter()
+        oracle.query(idx, wl.queries[done:done + k], wl.delta[done:done + k], threads=threads)
+        tq += time.perf_counter() - t1
+        done += k
+        if tq > left:
+            break
+        k *= 2
+    per_q = tq / done
+    t_full = tb + per_q * wl.m
+    return wl.m / t_full, {"build_s": tb, "queries_timed": done, "query_s": tq,
+                           "extrapolated_step_s": t_full}
+
+
+def cpu_baseline(wl, budget_s: float):
+    threads = os.cpu_count() or 1
+    v, det = oracle_sample(wl, budget_s, threads)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"oracle build (qsort, 1 thread) of all {wl.n} points + the first "
+                       f"{det['queries_timed']} of {wl.m} queries on {threads} threads; "
+                       f"queries/s of a whole step extrapolated from that sample"),
+            "detail": det}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workloads.mixed_1e7(scale=args.scale, seed=instance_seed(0))
+    threads = os.cpu_count() or 1
+    vals = []
+    det = None
+    for i in range(args.warmup + args.steps):
+        v, det = oracle_sample(wl, budget_s=6.0, threads=threads)
+        if i >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    t = wl.m / v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "n": wl.n, "m": wl.m, "curve": "z",
+                                           "bounds": "binary (std lower_bound)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": (f"per step: oracle build of all {wl.n} points + the first "
+                                       f"{det['queries_timed']} queries, extrapolated to {wl.m}")},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.gpus != world and world == 1 and args.gpus > 1:
+        print(json.dumps({"error": "run N>1 under torchrun"}), flush=True)
+        sys.exit(2)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,7 @@ typedef struct {
     int chunk;              /* scan chunk in points (0 = autotuned/default 1024) */
     int mask_budget_mb;     /* device memory for hit masks of the two-pass scan (default 1024) */
     int reorder_queries;    /* 1 = process queries in curve order for cache reuse (default 1) */
+    int profile;            /* 1 = record per-step CUDA events from the start (sfc_profile_read) */
 } sfc_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -169,6 +170,11 @@ sfc_status sfc_model_get(const sfc_index* idx, float* h_params, int* h_leaves,
                          uint32_t* h_first, uint32_t* h_end, float* h_slope, float* h_icpt,
                          int32_t* h_err_lo, int32_t* h_err_hi, void* stream);
 
+/* Work of the last query batch: points scanned (sum over queries of the interval lengths,
+ * the S_q of Alg. 1's scan loop), scan chunks, and points reported.  Synchronises. */
+sfc_status sfc_query_stats(const sfc_index* idx, uint64_t* h_scanned, uint64_t* h_chunks,
+                           uint64_t* h_hits, void* stream);
+
 /* Statistics of the last learned-bounds query batch: endpoints searched, endpoints whose
  * window missed (fell back to full binary search), and the sum of window lengths.
  * Synchronises. */
@@ -227,6 +233,22 @@ sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out,
 sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
                             uint64_t m, uint64_t* d_lo, uint64_t* d_hi, uint32_t* d_begin,
                             uint32_t* d_end, uint32_t* d_count, void* stream);
+
+/* Opt-in timing of the library's steps with CUDA events recorded on the launching stream
+ * around each step ("sort", "plan", "scan", "count", "write", "train", "update", ...).
+ * Enabling costs two event records per step; leave it off inside CUDA-graph capture. */
+typedef struct {
+    char name[24];
+    uint64_t launches;   /* times the step ran since the last reset */
+    double ms;           /* summed device time of those runs */
+} sfc_profile_entry;
+
+sfc_status sfc_profile_enable(sfc_index* idx, int on);
+
+/* Synchronises `stream`, aggregates the recorded steps by name into out[0..max) and
+ * writes how many entries there are to *count; reset != 0 clears the records. */
+sfc_status sfc_profile_read(sfc_index* idx, sfc_profile_entry* out, int max, int* count, int reset,
+                            void* stream);
 
 /* Number of this library's kernels launched by this process so far (host counter). */
 uint64_t sfc_launch_count(void);

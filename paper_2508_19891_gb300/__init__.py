@@ -46,7 +46,11 @@ class sfc_options(ctypes.Structure):
     _fields_ = [("bounds", ctypes.c_int), ("leaves", ctypes.c_int), ("train_steps", ctypes.c_int),
                 ("train_samples", ctypes.c_int), ("learning_rate", ctypes.c_float),
                 ("chunk", ctypes.c_int), ("mask_budget_mb", ctypes.c_int),
-                ("reorder_queries", ctypes.c_int)]
+                ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class sfc_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
 
 class SfcError(RuntimeError):
@@ -94,6 +98,9 @@ def lib():
             "sfc_exclusive_scan": (ci, [P, u64, P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
+            "sfc_query_stats": (ci, [P, P, P, P, P]),
+            "sfc_profile_enable": (ci, [P, ci]),
+            "sfc_profile_read": (ci, [P, P, ci, P, ci, P]),
             "sfc_status_string": (ctypes.c_char_p, [ci]),
         }
         for name, (res, args) in sig.items():
@@ -350,6 +357,26 @@ def sfc_model_stats(index: Index, stream=None):
     _check(lib().sfc_model_stats(index.handle, ctypes.byref(e), ctypes.byref(m), ctypes.byref(w),
                                  _stream(stream)), "sfc_model_stats")
     return {"endpoints": e.value, "misses": m.value, "window_sum": w.value}
+
+
+def sfc_query_stats(index: Index, stream=None):
+    s, g, h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().sfc_query_stats(index.handle, ctypes.byref(s), ctypes.byref(g), ctypes.byref(h),
+                                 _stream(stream)), "sfc_query_stats")
+    return {"scanned": s.value, "chunks": g.value, "hits": h.value}
+
+
+def sfc_profile_enable(index: Index, on: bool = True):
+    _check(lib().sfc_profile_enable(index.handle, int(bool(on))), "sfc_profile_enable")
+
+
+def sfc_profile_read(index: Index, reset: bool = True, stream=None) -> dict:
+    """{step name: (runs, total ms)} of the steps recorded since the last reset."""
+    buf = (sfc_profile_entry * 64)()
+    cnt = ctypes.c_int(0)
+    _check(lib().sfc_profile_read(index.handle, buf, 64, ctypes.byref(cnt), int(bool(reset)),
+                                  _stream(stream)), "sfc_profile_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(min(cnt.value, 64))}
 
 
 def sfc_update(index: Index, inserts: torch.Tensor | None, delete_ids: torch.Tensor | None,

@@ -2,6 +2,7 @@
 // workspaces, and the order of kernel launches for each call.  No computation of the method
 // happens here; every step runs in the kernels of keygen.cu, radix.cu, scan.cu, query.cu,
 // learned.cu and update.cu.
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -56,16 +57,19 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 sfc_status ensure_status_buf(sfc_index* idx, cudaStream_t st)
 {
     if (idx->status.ptr) return SFC_OK;
-    SFC_TRY(idx->status.ensure(sizeof(uint32_t) * 4 + sizeof(unsigned long long) * 4, st));
+    SFC_TRY(idx->status.ensure(16 + sizeof(unsigned long long) * 8, st));
     SFC_CUDA_TRY(cudaMemsetAsync(idx->status.ptr, 0, idx->status.bytes, st));
     return SFC_OK;
 }
 
 uint32_t* status_word(sfc_index* idx) { return idx->status.as<uint32_t>(); }
+// status buffer: u32 status word, padding, then u64 counters [0..2] learned-bounds
+// statistics, [3] points scanned by the last batch
 unsigned long long* model_stats(sfc_index* idx)
 {
     return reinterpret_cast<unsigned long long*>(idx->status.as<unsigned char>() + 16);
 }
+unsigned long long* scan_stats(sfc_index* idx) { return model_stats(idx) + 3; }
 
 sfc_status build_from_device(sfc_index* idx, const int32_t* d_points, cudaStream_t st)
 {
@@ -81,7 +85,10 @@ sfc_status build_from_device(sfc_index* idx, const int32_t* d_points, cudaStream
     dst.vals = idx->ids.as<uint32_t>();
     dst.xy = idx->xy.as<int2>();
     dst.curve = idx->curve;
-    SFC_TRY(radix_sort(src, n, dst, idx->sort_ws, status_word(idx), st));
+    {
+        ProfScope ps(idx, "sort", st);
+        SFC_TRY(radix_sort(src, n, dst, idx->sort_ws, status_word(idx), st));
+    }
     // the id -> coordinates table of the dynamic setting starts as a copy of the input
     SFC_TRY(idx->xy_by_id.ensure(n * sizeof(int2), st));
     if (n) SFC_CUDA_TRY(cudaMemcpyAsync(idx->xy_by_id.ptr, d_points, n * sizeof(int2),
@@ -153,13 +160,28 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.qbatch = idx->qbatch;
     a.work_ctr = w.ctr.as<unsigned long long>();
     a.out_offsets = d_out_offsets;
+    a.scanned = scan_stats(idx);
+    // per-batch statistics: learned-bounds counters and the scanned total
+    SFC_CUDA_TRY(cudaMemsetAsync(model_stats(idx), 0, 4 * sizeof(unsigned long long), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.counts, 0, m * sizeof(uint32_t), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, 4 * sizeof(unsigned long long), st));
     LearnedModelView lv;
-    SFC_TRY(launch_plan(a, model_view(idx, lv), st));
-    SFC_TRY(exclusive_scan_u32(a.nchunks, m, a.chunk_base, idx->scan_ws, a.status, st));
-    SFC_TRY(launch_count(a, st));
-    SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
+    {
+        ProfScope ps(idx, "plan", st);
+        SFC_TRY(launch_plan(a, model_view(idx, lv), st));
+    }
+    {
+        ProfScope ps(idx, "scan", st);
+        SFC_TRY(exclusive_scan_u32(a.nchunks, m, a.chunk_base, idx->scan_ws, a.status, st));
+    }
+    {
+        ProfScope ps(idx, "count", st);
+        SFC_TRY(launch_count(a, st));
+    }
+    {
+        ProfScope ps(idx, "scan", st);
+        SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
+    }
     w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk};
     return SFC_OK;
 }
@@ -187,6 +209,7 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.out_offsets = const_cast<uint64_t*>(d_out_offsets);
     a.out_ids = d_out_ids;
     a.ids_capacity = d_out_ids ? cap : 0;
+    ProfScope ps(idx, "write", st);
     return launch_write(a, st);
 }
 
@@ -205,6 +228,7 @@ void sfc_default_options(sfc_options* opt)
     opt->chunk = 0;
     opt->mask_budget_mb = 4096;
     opt->reorder_queries = 1;
+    opt->profile = 0;
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
@@ -231,6 +255,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     idx->bounds = SFC_BOUNDS_BINARY;
     idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;
     idx->last_stream = st;
+    idx->prof.on = o.profile != 0;
     sfc_status s = ensure_status_buf(idx, st);
     if (s == SFC_OK) s = build_from_device(idx, d_points, st);
     if (s == SFC_OK && o.bounds == SFC_BOUNDS_LEARNED) {
@@ -264,6 +289,11 @@ void sfc_destroy(sfc_index* idx)
 {
     if (!idx) return;
     cudaStream_t st = idx->last_stream;
+    for (const ProfRec& r : idx->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    idx->prof.recs.clear();
     release_index(idx, st);
     delete idx;
 }
@@ -348,7 +378,50 @@ sfc_status sfc_train_model(sfc_index* idx, void* stream)
 {
     if (!idx) return SFC_ERR_INVALID;
     idx->last_stream = as_stream(stream);
+    ProfScope ps(idx, "train", as_stream(stream));
     return train_model(idx, as_stream(stream));
+}
+
+sfc_status sfc_profile_enable(sfc_index* idx, int on)
+{
+    if (!idx) return SFC_ERR_INVALID;
+    idx->prof.on = on != 0;
+    return SFC_OK;
+}
+
+sfc_status sfc_profile_read(sfc_index* idx, sfc_profile_entry* out, int max, int* count, int reset,
+                            void* stream)
+{
+    if (!idx || (max > 0 && !out)) return SFC_ERR_INVALID;
+    SFC_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    std::vector<sfc_profile_entry> agg;
+    for (const ProfRec& r : idx->prof.recs) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.0f;
+        }
+        size_t k = 0;
+        while (k < agg.size() && std::strncmp(agg[k].name, r.name, sizeof(agg[k].name)) != 0) ++k;
+        if (k == agg.size()) {
+            sfc_profile_entry e{};
+            std::strncpy(e.name, r.name, sizeof(e.name) - 1);
+            agg.push_back(e);
+        }
+        agg[k].launches += 1;
+        agg[k].ms += ms;
+    }
+    if (reset) {
+        for (const ProfRec& r : idx->prof.recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        idx->prof.recs.clear();
+    }
+    const int n = (int)agg.size();
+    for (int i = 0; i < n && i < max; ++i) out[i] = agg[i];
+    if (count) *count = n;
+    return SFC_OK;
 }
 
 sfc_status sfc_model_stats(const sfc_index* cidx, uint64_t* h_endpoints, uint64_t* h_misses,
@@ -363,6 +436,28 @@ sfc_status sfc_model_stats(const sfc_index* cidx, uint64_t* h_endpoints, uint64_
     if (h_endpoints) *h_endpoints = v[0];
     if (h_misses) *h_misses = v[1];
     if (h_window_sum) *h_window_sum = v[2];
+    return SFC_OK;
+}
+
+sfc_status sfc_query_stats(const sfc_index* cidx, uint64_t* h_scanned, uint64_t* h_chunks,
+                           uint64_t* h_hits, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx || !idx->status.ptr) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    unsigned long long s = 0;
+    uint64_t g = 0, h = 0;
+    SFC_CUDA_TRY(cudaMemcpyAsync(&s, scan_stats(idx), sizeof(s), cudaMemcpyDeviceToHost, st));
+    const PendingCount& p = idx->qws.pending;
+    if (p.m && idx->qws.chunk_base.ptr)
+        SFC_CUDA_TRY(cudaMemcpyAsync(&g, idx->qws.chunk_base.as<uint64_t>() + p.m, sizeof(g),
+                                     cudaMemcpyDeviceToHost, st));
+    if (p.m && p.offsets)
+        SFC_CUDA_TRY(cudaMemcpyAsync(&h, p.offsets + p.m, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_scanned) *h_scanned = s;
+    if (h_chunks) *h_chunks = g;
+    if (h_hits) *h_hits = h;
     return SFC_OK;
 }
 

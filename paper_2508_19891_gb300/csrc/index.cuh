@@ -1,6 +1,8 @@
 // The opaque index object behind the C ABI and the host functions that operate on it.
 #pragma once
 
+#include <vector>
+
 #include "sfc_internal.cuh"
 
 namespace sfc {
@@ -32,6 +34,16 @@ struct ModelState {
     DevBuf scratch;                       // training samples, gradients, optimiser state
 };
 
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> recs;
+};
+
 struct UpdateWs {
     DevBuf a, b, c, d, e, f, g, h;
 };
@@ -61,6 +73,7 @@ struct sfc_index {
     sfc::HostStage stage;
     sfc::ModelState model;
     sfc::UpdateWs uws;
+    sfc::Profiler prof;
 };
 
 namespace sfc {
@@ -68,5 +81,30 @@ namespace sfc {
 sfc_status ensure_alive_bits(sfc_index* idx, uint64_t ids, cudaStream_t st);
 void release_index(sfc_index* idx, cudaStream_t st);
 sfc_status train_model(sfc_index* idx, cudaStream_t st);
+
+// Records CUDA events around a step when profiling is on.
+class ProfScope {
+public:
+    ProfScope(sfc_index* idx, const char* name, cudaStream_t st) : idx_(idx), st_(st)
+    {
+        if (!idx || !idx->prof.on) return;
+        rec_.name = name;
+        if (cudaEventCreate(&rec_.a) != cudaSuccess) return;
+        if (cudaEventCreate(&rec_.b) != cudaSuccess) { cudaEventDestroy(rec_.a); return; }
+        cudaEventRecord(rec_.a, st);
+        live_ = true;
+    }
+    ~ProfScope()
+    {
+        if (!live_) return;
+        cudaEventRecord(rec_.b, st_);
+        idx_->prof.recs.push_back(rec_);
+    }
+private:
+    sfc_index* idx_;
+    cudaStream_t st_;
+    ProfRec rec_{};
+    bool live_ = false;
+};
 
 }  // namespace sfc

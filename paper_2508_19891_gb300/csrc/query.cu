@@ -228,10 +228,16 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(QueryArgs a, Bounds boun
     // every lane calls the bound search (with no endpoints when inactive or invalid), so
     // warp-collective statistics inside it see a converged warp
     query_bounds(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, R, b, e);
-    if (!active) return;
     uint64_t S = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) S += e[k] - b[k];
+    if (a.scanned) {   // one atomic per warp
+        unsigned long long ws = S;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        if (lane_id() == 0 && ws) atomicAdd(a.scanned, ws);
+    }
+    if (!active) return;
     uint4* rp = reinterpret_cast<uint4*>(a.ranges + 8 * i);
     rp[0] = make_uint4(b[0], e[0], b[1], e[1]);
     rp[1] = make_uint4(b[2], e[2], b[3], e[3]);

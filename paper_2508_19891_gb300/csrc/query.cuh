@@ -28,6 +28,7 @@ struct QueryArgs {
     uint32_t* out_ids;
     uint64_t ids_capacity;
     uint32_t* status;
+    unsigned long long* scanned;   // sum of S_q over the batch (statistics)
 };
 
 struct LearnedModelView {
