@@ -51,6 +51,9 @@ typedef enum {
 
 typedef enum { SFC_CURVE_Z = 0, SFC_CURVE_HILBERT = 1 } sfc_curve;
 typedef enum { SFC_BOUNDS_BINARY = 0, SFC_BOUNDS_LEARNED = 1 } sfc_bounds;
+/* Root of the learned CDF model: monotone piecewise linear over 256 equal key intervals
+ * (the key ranges of the level-4 quadtree cells), or a 1-16-1 monotone sigmoid MLP. */
+typedef enum { SFC_ROOT_PWL = 0, SFC_ROOT_MLP = 1 } sfc_root;
 
 /* Device status bits (sfc_device_status_bits). */
 #define SFC_DEV_BAD_POINT   0x1u   /* a point coordinate outside [0, 2^30) */
@@ -71,6 +74,7 @@ typedef struct {
     int mask_budget_mb;     /* device memory for hit masks of the two-pass scan (default 1024) */
     int reorder_queries;    /* 1 = process queries in curve order for cache reuse (default 1) */
     int profile;            /* 1 = record per-step CUDA events from the start (sfc_profile_read) */
+    sfc_root root;          /* learned model: root kind (default SFC_ROOT_PWL) */
 } sfc_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -148,25 +152,33 @@ sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);
  * the leaf least-squares lines and the exact per-leaf error windows. */
 sfc_status sfc_train_model(sfc_index* idx, void* stream);
 
-/* Number of root hidden units H; the root has 3H + 1 parameters (alpha[H], beta[H], b[H], c). */
+/* Number of MLP root hidden units H (the MLP root has 3H + 1 parameters: alpha[H], beta[H],
+ * b[H], c; f(x) = c + sum_k exp(alpha_k) sigmoid(exp(beta_k) x + b_k)). */
 int sfc_model_hidden(void);
 
-/* Loss and gradient of the root for given parameters on given samples (the training kernels
- * run once, no update): h_params float[3H+1] (host), d_keys uint64[s] (device, sample keys),
- * d_y float[s] (device, target normalised ranks).  Writes *h_loss and h_grad float[3H+1]
- * (host).  Synchronises `stream`. */
-sfc_status sfc_model_loss_grad(const float* h_params, const uint64_t* d_keys, const float* d_y,
-                               uint64_t s, float* h_loss, float* h_grad, void* stream);
+/* Number of parameters of a root kind: MLP 3H + 1; piecewise linear K + 1 = 257
+ * (d[K] log-increments then c; knot heights h_0 = c, h_{k+1} = h_k + exp(d_k)); -1 if unknown. */
+int sfc_model_params(sfc_root root);
 
-/* One Adam step of the device optimiser on host-given state (for tests): updates h_params,
- * h_m, h_v (float[3H+1] each) in place with gradient h_grad at step t >= 1. */
-sfc_status sfc_model_adam_step(float* h_params, float* h_m, float* h_v, const float* h_grad,
+/* Mean-squared error of the root on samples (x = key / 2^60, target y) and its gradient, from
+ * the training kernels run once with no update: h_params float[sfc_model_params(root)]
+ * (host), d_keys uint64[s] (device), d_y float[s] (device).  Writes *h_loss and
+ * h_grad float[sfc_model_params(root)] (host).  Synchronises `stream`. */
+sfc_status sfc_model_loss_grad(sfc_root root, const float* h_params, const uint64_t* d_keys,
+                               const float* d_y, uint64_t s, float* h_loss, float* h_grad,
+                               void* stream);
+
+/* One step of the device Adam optimiser (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
+ * on host-given state of np parameters: updates h_params, h_m, h_v in place with gradient
+ * h_grad at step t >= 1.  Synchronises. */
+sfc_status sfc_model_adam_step(float* h_params, float* h_m, float* h_v, const float* h_grad, int np,
                                int t, float lr, void* stream);
 
-/* Copies the trained model out (host): root parameters float[3H+1]; per leaf j < leaves:
- * first position, end position, slope, intercept, err_lo, err_hi.  Any pointer may be NULL.
- * *h_leaves receives the leaf count.  Synchronises. */
-sfc_status sfc_model_get(const sfc_index* idx, float* h_params, int* h_leaves,
+/* Copies the trained model out (host): the root kind, its parameters
+ * (float[sfc_model_params(kind)]); per leaf j < *h_leaves: first position, end position,
+ * slope, intercept, err_lo, err_hi.  Any pointer may be NULL.  SFC_ERR_STATE if no model.
+ * Synchronises. */
+sfc_status sfc_model_get(const sfc_index* idx, int* h_root, float* h_params, int* h_leaves,
                          uint32_t* h_first, uint32_t* h_end, float* h_slope, float* h_icpt,
                          int32_t* h_err_lo, int32_t* h_err_hi, void* stream);
 

@@ -1,5 +1,9 @@
 """fp64 reference of the learned-bounds model (TEST INFRASTRUCTURE ONLY; see oracle/__init__).
 
+Two root kinds are referenced here: the 1 -> H -> 1 monotone MLP below, and the
+piecewise-linear root (``pwl_*``): K knots at x = k / K whose heights theta = (h_0 .. h_K)
+are the parameters (kept non-decreasing by the optimiser's projection).
+
 The paper accelerates ``A_P.lower_bound`` (Alg. 1) with a static S-tree over the key array
 (Sec. 2.1, "Storing P twice").  The GPU path replaces that search structure by a two-stage
 learned CDF model whose prediction is only a hint: every predicted position is verified and
@@ -100,6 +104,54 @@ def adam_step(theta, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=
     vhat = v / (1.0 - beta2 ** t)
     theta = theta - lr * mhat / (np.sqrt(vhat) + eps)
     return theta, m, v
+
+
+# --------------------------------------------------------------------------------------
+# piecewise-linear root
+# --------------------------------------------------------------------------------------
+
+def pwl_forward(theta, x, K: int):
+    """f(x) = h_k + (h_{k+1} - h_k) t with s = x K, k = min(floor(s), K - 1), t = s - k."""
+    h = np.asarray(theta, np.float64)
+    assert h.shape == (K + 1,)
+    s = np.asarray(x, np.float64) * K
+    k = np.clip(np.floor(s).astype(np.int64), 0, K - 1)
+    t = s - k
+    return h[k] + (h[k + 1] - h[k]) * t
+
+
+def pwl_loss(theta, x, y, K: int) -> float:
+    r = pwl_forward(theta, x, K) - np.asarray(y, np.float64)
+    return float(np.mean(r * r))
+
+
+def pwl_loss_grad(theta, x, y, K: int):
+    """Loss and analytic gradient: with r_i = 2 (f_i - y_i) / N, knot k_i receives
+    r_i (1 - t_i) and knot k_i + 1 receives r_i t_i."""
+    h = np.asarray(theta, np.float64)
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    N = x.shape[0]
+    s = x * K
+    k = np.clip(np.floor(s).astype(np.int64), 0, K - 1)
+    t = s - k
+    f = h[k] + (h[k + 1] - h[k]) * t
+    res = f - y
+    r = 2.0 * res / N
+    g = np.zeros(K + 1)
+    np.add.at(g, k, r * (1.0 - t))
+    np.add.at(g, k + 1, r * t)
+    return float(np.mean(res * res)), g
+
+
+def pwl_init(K: int) -> np.ndarray:
+    """Heights k / K: f(x) = x."""
+    return np.arange(K + 1, dtype=np.float64) / K
+
+
+def pwl_project(theta) -> np.ndarray:
+    """Running maximum: the nearest-above non-decreasing sequence used after each step."""
+    return np.maximum.accumulate(np.asarray(theta, np.float64))
 
 
 def leaf_fit(u: np.ndarray, v: np.ndarray):

@@ -34,6 +34,8 @@ SFC_CURVE_Z = 0
 SFC_CURVE_HILBERT = 1
 SFC_BOUNDS_BINARY = 0
 SFC_BOUNDS_LEARNED = 1
+SFC_ROOT_PWL = 0
+SFC_ROOT_MLP = 1
 
 SFC_DEV_BAD_POINT = 0x1
 SFC_DEV_BAD_QUERY = 0x2
@@ -46,7 +48,7 @@ class sfc_options(ctypes.Structure):
     _fields_ = [("bounds", ctypes.c_int), ("leaves", ctypes.c_int), ("train_steps", ctypes.c_int),
                 ("train_samples", ctypes.c_int), ("learning_rate", ctypes.c_float),
                 ("chunk", ctypes.c_int), ("mask_budget_mb", ctypes.c_int),
-                ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int), ("root", ctypes.c_int)]
 
 
 class sfc_profile_entry(ctypes.Structure):
@@ -85,9 +87,10 @@ def lib():
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_train_model": (ci, [P, P]),
             "sfc_model_hidden": (ci, []),
-            "sfc_model_loss_grad": (ci, [P, P, P, u64, P, P, P]),
-            "sfc_model_adam_step": (ci, [P, P, P, P, ci, ctypes.c_float, P]),
-            "sfc_model_get": (ci, [P, P, P, P, P, P, P, P, P, P]),
+            "sfc_model_params": (ci, [ci]),
+            "sfc_model_loss_grad": (ci, [ci, P, P, P, u64, P, P, P]),
+            "sfc_model_adam_step": (ci, [P, P, P, P, ci, ci, ctypes.c_float, P]),
+            "sfc_model_get": (ci, [P, P, P, P, P, P, P, P, P, P, P]),
             "sfc_model_stats": (ci, [P, P, P, P, P]),
             "sfc_update": (ci, [P, P, u64, P, u64, P, P]),
             "sfc_get_sorted": (ci, [P, PP, PP, PP, ctypes.POINTER(ctypes.c_uint64)]),
@@ -173,12 +176,22 @@ def sfc_status_string(status: int) -> str:
     return lib().sfc_status_string(int(status)).decode()
 
 
+def _root(r):
+    if r in (SFC_ROOT_PWL, "pwl"):
+        return SFC_ROOT_PWL
+    if r in (SFC_ROOT_MLP, "mlp"):
+        return SFC_ROOT_MLP
+    raise ValueError(f"unknown root kind {r!r}")
+
+
 def sfc_default_options(**overrides) -> sfc_options:
     o = sfc_options()
     lib().sfc_default_options(ctypes.byref(o))
     for k, v in overrides.items():
         if k == "bounds":
             v = _bounds(v)
+        if k == "root":
+            v = _root(v)
         setattr(o, k, v)
     return o
 
@@ -314,13 +327,17 @@ def sfc_model_hidden() -> int:
     return int(lib().sfc_model_hidden())
 
 
-def sfc_model_loss_grad(params: np.ndarray, keys: torch.Tensor, y: torch.Tensor, stream=None):
-    H = sfc_model_hidden()
+def sfc_model_params(root="pwl") -> int:
+    return int(lib().sfc_model_params(_root(root)))
+
+
+def sfc_model_loss_grad(params: np.ndarray, keys: torch.Tensor, y: torch.Tensor, root="pwl", stream=None):
+    npar = sfc_model_params(root)
     p = np.ascontiguousarray(params, np.float32)
-    assert p.shape == (3 * H + 1,)
+    assert p.shape == (npar,)
     loss = np.zeros(1, np.float32)
-    grad = np.zeros(3 * H + 1, np.float32)
-    _check(lib().sfc_model_loss_grad(_hptr(p), _dptr(keys), _dptr(y), keys.numel(), _hptr(loss),
+    grad = np.zeros(npar, np.float32)
+    _check(lib().sfc_model_loss_grad(_root(root), _hptr(p), _dptr(keys), _dptr(y), keys.numel(), _hptr(loss),
                                      _hptr(grad), _stream(stream)), "sfc_model_loss_grad")
     return float(loss[0]), grad
 
@@ -330,22 +347,23 @@ def sfc_model_adam_step(params, m, v, grad, t: int, lr: float, stream=None):
     mm = np.array(m, np.float32)
     vv = np.array(v, np.float32)
     g = np.ascontiguousarray(grad, np.float32)
-    _check(lib().sfc_model_adam_step(_hptr(p), _hptr(mm), _hptr(vv), _hptr(g), int(t), float(lr),
+    _check(lib().sfc_model_adam_step(_hptr(p), _hptr(mm), _hptr(vv), _hptr(g), p.size, int(t), float(lr),
                                      _stream(stream)), "sfc_model_adam_step")
     return p, mm, vv
 
 
 def sfc_model_get(index: Index, stream=None) -> dict:
-    H = sfc_model_hidden()
     nl = ctypes.c_int(0)
-    _check(lib().sfc_model_get(index.handle, None, ctypes.byref(nl), None, None, None, None, None,
-                               None, _stream(stream)), "sfc_model_get")
+    kind = ctypes.c_int(0)
+    _check(lib().sfc_model_get(index.handle, ctypes.byref(kind), None, ctypes.byref(nl), None, None, None, None,
+                               None, None, _stream(stream)), "sfc_model_get")
     L = nl.value
-    out = {"params": np.zeros(3 * H + 1, np.float32), "first": np.zeros(L, np.uint32),
+    out = {"root": "mlp" if kind.value == SFC_ROOT_MLP else "pwl",
+           "params": np.zeros(sfc_model_params(kind.value), np.float32), "first": np.zeros(L, np.uint32),
            "end": np.zeros(L, np.uint32), "slope": np.zeros(L, np.float32),
            "icpt": np.zeros(L, np.float32), "err_lo": np.zeros(L, np.int32),
            "err_hi": np.zeros(L, np.int32)}
-    _check(lib().sfc_model_get(index.handle, _hptr(out["params"]), ctypes.byref(nl),
+    _check(lib().sfc_model_get(index.handle, None, _hptr(out["params"]), ctypes.byref(nl),
                                _hptr(out["first"]), _hptr(out["end"]), _hptr(out["slope"]),
                                _hptr(out["icpt"]), _hptr(out["err_lo"]), _hptr(out["err_hi"]),
                                _stream(stream)), "sfc_model_get")

@@ -131,7 +131,7 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
 const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
 {
     if (idx->bounds != SFC_BOUNDS_LEARNED || !idx->model.trained) return nullptr;
-    v.root = idx->model.root;
+    v.root = model_root_device(idx);
     v.leaf = idx->model.leaves.as<LeafParams>();
     v.stats = model_stats(idx);
     return &v;
@@ -229,6 +229,7 @@ void sfc_default_options(sfc_options* opt)
     opt->mask_budget_mb = 4096;
     opt->reorder_queries = 1;
     opt->profile = 0;
+    opt->root = SFC_ROOT_PWL;
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
@@ -243,7 +244,8 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     if (opt) o = *opt;
     if (o.leaves < 1 || o.leaves > (1 << 20) || o.mask_budget_mb < 1 || o.train_samples < 2 ||
         o.train_steps < 0 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
-        (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED))
+        (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED) ||
+        (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP))
         return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     sfc_index* idx = new (std::nothrow) sfc_index();

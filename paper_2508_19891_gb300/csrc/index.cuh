@@ -28,10 +28,13 @@ struct HostStage {          // device staging of sfc_query_batch_host
 struct ModelState {
     bool trained = false;
     int nleaves = 0;
-    RootParams root{};                    // derived parameters used by the predict path
-    float theta[3 * kHidden + 1] = {};    // trained (alpha, beta, b, c)
-    DevBuf leaves;                        // LeafParams[nleaves]
-    DevBuf scratch;                       // training samples, gradients, optimiser state
+    int kind = 0;      // root kind of the trained model
+    DevBuf state;      // optimiser state and derived root parameters (layout in learned.cu)
+    DevBuf samples;    // training sample x[N], y[N]
+    DevBuf partial;    // per-block partial gradients and the completion counter
+    DevBuf tmp;        // per-leaf first/last position and error extremes during a fit
+    DevBuf leaves;     // LeafParams[nleaves], read by the query path
+    DevBuf route;      // leaf of every key (uint32[n])
 };
 
 struct ProfRec {
@@ -45,7 +48,9 @@ struct Profiler {
 };
 
 struct UpdateWs {
-    DevBuf a, b, c, d, e, f, g, h;
+    DevBuf a, b, c, d, e, f, g, h;   // flags, delete keys/ids/positions, insert keys/ids/xy/ranks
+    DevBuf keys, ids, xy;            // the next sorted arrays (swapped with the index's)
+    DevBuf mark, v, t;               // deleted marks, shift counts, their exclusive scan
 };
 
 }  // namespace sfc
@@ -81,6 +86,11 @@ namespace sfc {
 sfc_status ensure_alive_bits(sfc_index* idx, uint64_t ids, cudaStream_t st);
 void release_index(sfc_index* idx, cudaStream_t st);
 sfc_status train_model(sfc_index* idx, cudaStream_t st);
+sfc_status fit_leaves(sfc_index* idx, cudaStream_t st);
+sfc_status refit_model(sfc_index* idx, int steps, cudaStream_t st);
+sfc_status apply_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins, const uint32_t* d_del,
+                        uint64_t k_del, uint32_t* h_first, cudaStream_t st);
+const RootParams* model_root_device(sfc_index* idx);
 
 // Records CUDA events around a step when profiling is on.
 class ProfScope {

@@ -108,6 +108,7 @@ __device__ __forceinline__ void lower_bounds_window(const uint64_t* __restrict__
 }
 
 struct BinaryBounds {
+    __device__ __forceinline__ void prepare(RootParams*) {}
     __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
                                                uint32_t* r, int ne) const
     {
@@ -121,9 +122,17 @@ struct BinaryBounds {
 };
 
 struct LearnedBounds {
-    RootParams root;
+    const RootParams* root;      // device; after prepare() the block's shared-memory copy
     const LeafParams* leaf;
     unsigned long long* stats;   // [0] endpoints, [1] misses, [2] window sum
+    // every thread of the block calls this, then the block synchronises
+    __device__ __forceinline__ void prepare(RootParams* s)
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(root);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(s);
+        for (unsigned i = threadIdx.x; i < sizeof(RootParams) / 4; i += blockDim.x) dst[i] = src[i];
+        root = s;
+    }
     __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
                                                uint32_t* r, int ne) const
     {
@@ -134,7 +143,7 @@ struct LearnedBounds {
             lo[e] = 0;
             len[e] = 0;
             if (e < ne) {
-                const int j = route_leaf(root, t[e]);
+                const int j = route_leaf(*root, t[e]);
                 const LeafParams lp = leaf[j];
                 const int64_t p = leaf_predict(lp, t[e]);
                 int64_t a = p + lp.err_lo, b = p + (int64_t)lp.err_hi + 1;
@@ -209,9 +218,13 @@ __device__ __forceinline__ int query_bounds(const Bounds& bounds, int curve, con
 // plan_kernel
 // ------------------------------------------------------------------------------------
 template <class Bounds>
-__global__ void __launch_bounds__(kThreads) plan_kernel(QueryArgs a, Bounds bounds)
+__global__ void __launch_bounds__(kThreads) plan_kernel(QueryArgs a, Bounds bounds_in)
 {
     __shared__ HilbertTables tb;
+    __shared__ RootParams s_root;
+    Bounds bounds = bounds_in;
+    bounds.prepare(&s_root);
+    __syncthreads();
     if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = i < a.m;
@@ -275,14 +288,27 @@ __device__ __forceinline__ uint32_t map_pos(const QView& v, uint32_t f)
     return f < v.c1 ? v.b0 + f : f < v.c2 ? v.b1 + (f - v.c1) : f < v.c3 ? v.b2 + (f - v.c2) : v.b3 + (f - v.c3);
 }
 
+// Offset from concatenated index f to array position (mod 2^32) for the interval holding f,
+// and the first concatenated index of the next interval.
+__device__ __forceinline__ void interval_of(const QView& v, uint32_t f, uint32_t& shift, uint32_t& end)
+{
+    shift = f < v.c1 ? v.b0 : f < v.c2 ? v.b1 - v.c1 : f < v.c3 ? v.b2 - v.c2 : v.b3 - v.c3;
+    end = f < v.c1 ? v.c1 : f < v.c2 ? v.c2 : f < v.c3 ? v.c3 : 0xffffffffu;
+}
+
+// Exact closed-ball test: |dx|, |dy| < 2^30, so each square is one signed 32x32 -> 64-bit
+// multiply(-add) and the sum stays below 2^61.
 __device__ __forceinline__ bool is_hit(const QView& v, int2 p)
 {
-    const int64_t dx = (int64_t)p.x - v.q.x, dy = (int64_t)p.y - v.q.y;
-    return dx * dx + dy * dy <= v.d2;
+    const int dx = p.x - v.q.x, dy = p.y - v.q.y;
+    const long long s = (long long)dx * dx + (long long)dy * dy;
+    return s <= v.d2;
 }
 
 // Filters points [s0, s1) of the query's concatenated intervals; returns the hit count and
-// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.
+// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.  Each
+// lane advances its array position by 32 per word and looks the interval up again only when
+// it crosses into the next one.
 template <int WPL>
 __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, uint32_t s0,
                                                  uint32_t s1, uint32_t (&words)[WPL])
@@ -293,14 +319,18 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
     uint32_t cnt = 0;
     const uint32_t nit = (s1 - s0 + 31) >> 5;
     const int2* __restrict__ xy = a.xy;
+    uint32_t f = s0 + lane;
+    uint32_t shift, end;
+    interval_of(v, f, shift, end);
     for (uint32_t it = 0; it < nit; it += 4) {
         int2 p[4];
         bool val[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t f = s0 + ((it + u) << 5) + lane;
-            val[u] = f < s1;
-            p[u] = val[u] ? __ldcs(xy + map_pos(v, f)) : make_int2(0, 0);
+            const uint32_t fu = f + 32u * u;
+            val[u] = fu < s1;
+            if (fu >= end) interval_of(v, fu, shift, end);
+            p[u] = val[u] ? __ldg(xy + (fu + shift)) : make_int2(0, 0);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -311,8 +341,20 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
             for (int s = 0; s < WPL; ++s)
                 if (wi == (uint32_t)(s * 32) + lane) words[s] = w;
         }
+        f += 128;
     }
     return cnt;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v += t;
+    }
+    return v;
 }
 
 // Warp-cooperative search: the query owning chunk g (largest q with base[q] <= g).
@@ -378,8 +420,10 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 template <int WPL>
 __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
 {
+    // per-warp staging of the array positions of one group of 32 mask words (<= 1024 hits)
+    __shared__ uint32_t s_pos[kThreads / 32][1024];
+    uint32_t* buf = s_pos[threadIdx.x >> 5];
     const unsigned lane = lane_id();
-    const uint32_t lt = lanemask_lt();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
         set_status(a.status, SFC_DEV_CAPACITY);
     const uint32_t W = a.chunk >> 5;
@@ -413,19 +457,32 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                 } else {
                     filter_chunk<WPL>(a, v, s0, s1, words);
                 }
-                for (uint32_t wi = 0; wi < nw; ++wi) {
-                    uint32_t mine = words[0];
 #pragma unroll
-                    for (int s = 1; s < WPL; ++s)
-                        if ((wi >> 5) == (uint32_t)s) mine = words[s];
-                    const uint32_t w = __shfl_sync(0xffffffffu, mine, wi & 31);
-                    if (w == 0) continue;
-                    if ((w >> lane) & 1u) {
-                        const uint32_t pos = map_pos(v, s0 + (wi << 5) + lane);
-                        const uint64_t dst = off + rank + __popc(w & lt);
-                        if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
+                for (int s = 0; s < WPL; ++s) {
+                    const uint32_t wl = words[s];
+                    const uint32_t pc = __popc(wl);
+                    const uint32_t incl = warp_incl_scan_u32(pc);
+                    const uint32_t K = __shfl_sync(0xffffffffu, incl, 31);
+                    if (K == 0) continue;
+                    // each lane lists the positions of its own word's hits
+                    uint32_t slot = incl - pc;
+                    uint32_t bits = wl;
+                    const uint32_t fbase = s0 + ((uint32_t)(s * 32) + lane) * 32u;
+                    while (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        buf[slot++] = map_pos(v, fbase + (uint32_t)b);
                     }
-                    rank += __popc(w);
+                    __syncwarp();
+                    // coalesced gather of the ids and write of the output
+                    const uint64_t dst0 = off + rank;
+                    for (uint32_t t = lane; t < K; t += 32) {
+                        const uint64_t dst = dst0 + t;
+                        const uint32_t id = __ldg(a.ids + buf[t]);
+                        if (dst < a.ids_capacity) a.out_ids[dst] = id;
+                    }
+                    __syncwarp();
+                    rank += K;
                 }
             }
         }
@@ -436,11 +493,15 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
 // ranges export (tests)
 // ------------------------------------------------------------------------------------
 template <class Bounds>
-__global__ void __launch_bounds__(kThreads) ranges_kernel(QueryArgs a, Bounds bounds, uint64_t* out_lo,
+__global__ void __launch_bounds__(kThreads) ranges_kernel(QueryArgs a, Bounds bounds_in, uint64_t* out_lo,
                                                           uint64_t* out_hi, uint32_t* out_b,
                                                           uint32_t* out_e, uint32_t* out_cnt)
 {
     __shared__ HilbertTables tb;
+    __shared__ RootParams s_root;
+    Bounds bounds = bounds_in;
+    bounds.prepare(&s_root);
+    __syncthreads();
     if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = i < a.m;

@@ -32,7 +32,7 @@ struct QueryArgs {
 };
 
 struct LearnedModelView {
-    RootParams root;
+    const RootParams* root;      // device memory (written by training, no host copy needed)
     const LeafParams* leaf;
     unsigned long long* stats;   // [3]: endpoints, misses, window sum
 };

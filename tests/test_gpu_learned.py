@@ -1,0 +1,175 @@
+"""GPU learned bounds: the training kernels against the fp64 oracle (gradient, Adam step),
+and the learned bound search against binary search (bit-exact positions and outputs)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import learned as OL
+import paper_2508_19891_gb300 as sfc
+import workloads as W
+from conftest import to_dev, u32, u64
+
+pytestmark = pytest.mark.gpu
+
+H = 16
+
+
+def _sample(keys_sorted, s):
+    n = keys_sorted.shape[0]
+    i = (np.arange(s, dtype=np.float64) * n / s).astype(np.int64)
+    return keys_sorted[i], (i / n)
+
+
+K = 256
+
+
+@pytest.mark.parametrize("root", ["mlp", "pwl"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gradient_matches_fp64_oracle(cuda, root, seed):
+    """The training kernels' loss and gradient against the fp64 analytic reference (itself
+    pinned by finite differences), relative tolerance 1e-3 (fp32 accumulation)."""
+    assert sfc.sfc_model_hidden() == H
+    assert sfc.sfc_model_params("mlp") == 3 * H + 1 and sfc.sfc_model_params("pwl") == K + 1
+    wl = (W.mixed_1e7(scale=0.01, seed=seed + 10) if seed != 2
+          else W.normal_uniform_queries(100_000, 1, 0.001))
+    ref = oracle.build(wl.points)
+    k, y = _sample(ref.keys, 4096)
+    rng = np.random.default_rng(seed)
+    x = k.astype(np.float64) / 2.0 ** 60
+    y32 = y.astype(np.float32).astype(np.float64)
+    if root == "mlp":
+        theta = (OL.init_params(H) + rng.normal(0, 0.3, 3 * H + 1)).astype(np.float32)
+        rloss, rg = OL.root_loss_grad(theta.astype(np.float64), x, y32, H)
+    else:
+        theta = OL.pwl_project(OL.pwl_init(K) + rng.normal(0, 0.01, K + 1)).astype(np.float32)
+        rloss, rg = OL.pwl_loss_grad(theta.astype(np.float64), x, y32, K)
+    loss, g = sfc.sfc_model_loss_grad(theta, to_dev(k.view(np.int64), cuda),
+                                      to_dev(y.astype(np.float32), cuda), root=root)
+    assert loss == pytest.approx(rloss, rel=1e-3)
+    scale = np.abs(rg).max()
+    np.testing.assert_allclose(g, rg, rtol=1e-3, atol=1e-3 * scale)
+
+
+@pytest.mark.parametrize("npar", [3 * H + 1, K + 1])
+def test_adam_step_matches_oracle(cuda, npar):
+    rng = np.random.default_rng(4)
+    th = rng.normal(0, 1, npar)
+    m = rng.normal(0, 0.1, npar)
+    v = np.abs(rng.normal(0, 0.1, npar))
+    g = rng.normal(0, 1, npar)
+    for t in (1, 2, 50):
+        p, mm, vv = sfc.sfc_model_adam_step(th, m, v, g, t, 0.02)
+        rp, rm, rv = OL.adam_step(th, g, m, v, t, 0.02)
+        np.testing.assert_allclose(mm, rm, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(vv, rv, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(p, rp, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("root", ["mlp", "pwl"])
+def test_training_lowers_the_loss(cuda, root):
+    wl = W.normal_uniform_queries(200_000, 1, 0.001)
+    idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned", root=root)
+    model = sfc.sfc_model_get(idx)
+    assert model["root"] == root
+    ref = oracle.build(wl.points)
+    k, y = _sample(ref.keys, 65536)
+    x = k.astype(np.float64) / 2.0 ** 60
+    p = model["params"].astype(np.float64)
+    if root == "mlp":
+        trained, initial = OL.root_loss(p, x, y, H), OL.root_loss(OL.init_params(H), x, y, H)
+    else:
+        trained, initial = OL.pwl_loss(p, x, y, K), OL.pwl_loss(OL.pwl_init(K), x, y, K)
+    assert trained < 0.5 * initial, (trained, initial)
+    # leaves tile the array: first/end are monotone and cover [0, n)
+    first, end = model["first"].astype(np.int64), model["end"].astype(np.int64)
+    assert first[0] == 0 and end[-1] == wl.n
+    assert np.all(end >= first) and np.all(first[1:] == end[:-1])
+
+
+@pytest.mark.parametrize("root", ["pwl", "mlp"])
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("make", ["uniform", "mixed", "dups", "tiny", "normal"])
+def test_learned_equals_binary(cuda, curve, make, root):
+    if make == "uniform":
+        wl = W.uniform_1e5()
+        pts, qs, d = wl.points, wl.queries, wl.delta
+    elif make == "mixed":
+        wl = W.mixed_1e7(scale=0.02)
+        pts, qs, d = wl.points, wl.queries, wl.delta
+    elif make == "dups":
+        pts, qs, d = W.tiny_dense(3, 20000, 3000, 6, 10)
+    elif make == "normal":
+        wl = W.normal_uniform_queries(100_000, 5000, 0.003)
+        pts, qs, d = wl.points, wl.queries, wl.delta
+    else:
+        pts, qs, d = W.tiny_dense(4, 3, 500, 30, 1 << 20)
+    idx = sfc.sfc_build(to_dev(pts, cuda), curve, bounds="learned", leaves=512, root=root)
+    qt, dt = to_dev(qs, cuda), to_dev(d, cuda)
+    lo, hi, bl, el, cl = sfc.sfc_query_ranges(idx, qt, dt)
+    offl, idsl = sfc.query(idx, qt, dt)
+    stats = sfc.sfc_model_stats(idx)
+    sfc.sfc_set_bounds_mode(idx, "binary")
+    lo2, hi2, bb, eb, cb = sfc.sfc_query_ranges(idx, qt, dt)
+    offb, idsb = sfc.query(idx, qt, dt)
+    assert torch.equal(cl, cb) and torch.equal(lo, lo2) and torch.equal(hi, hi2)
+    assert torch.equal(bl, bb) and torch.equal(el, eb)
+    assert torch.equal(offl, offb) and torch.equal(idsl, idsb)
+    ref = oracle.build(pts, 30, curve)
+    roff, rids = oracle.query(ref, qs, d)
+    assert np.array_equal(u64(offl), roff) and np.array_equal(u32(idsl), rids)
+    # the window misses at most a sliver of endpoints (they fall back to binary search)
+    assert stats["endpoints"] > 0
+    assert stats["misses"] <= 0.01 * stats["endpoints"] + 2, stats
+    assert sfc.sfc_device_status(idx) == (0, 0)
+
+
+def test_learned_on_empty_and_single(cuda):
+    for n in (0, 1, 2):
+        pts = np.array([[5, 9], [5, 9]][:n], np.int32).reshape(-1, 2)
+        idx = sfc.sfc_build(to_dev(pts, cuda), "z", bounds="learned")
+        q = to_dev(np.array([[5, 9], [0, 0]], np.int32), cuda)
+        d = to_dev(np.array([0, 3], np.int32), cuda)
+        off, ids = sfc.query(idx, q, d)
+        assert off.tolist() == [0, n, n]
+
+
+def test_learned_search_gain_over_binary(cuda):
+    """What the learned model gains over the method without it (full binary search over the
+    keys, Alg. 1's lower_bound): the search per endpoint runs over the stored error window
+    instead of all n keys, so the dependent probes per endpoint drop from log2(n + 1) to about
+    log2(window + 1), with identical positions (test_learned_equals_binary)."""
+    for wl in (W.normal_uniform_queries(1_000_000, 50_000, 0.001), W.mixed_1e7(scale=0.1)):
+        pts, qt, dt = to_dev(wl.points, cuda), to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
+        idx = sfc.sfc_build(pts, "z", bounds="learned")
+        sfc.query(idx, qt, dt)
+        st = sfc.sfc_model_stats(idx)
+        window = st["window_sum"] / st["endpoints"]
+        probes_learned = np.log2(window + 1)
+        probes_binary = np.log2(wl.n + 1)
+        print(wl.name, "mean window", window, "probes", probes_learned, "vs", probes_binary,
+              "misses", st["misses"])
+        assert window < wl.n / 100
+        assert probes_learned < 0.5 * probes_binary
+        assert st["misses"] <= 0.01 * st["endpoints"]
+
+
+def test_trained_vs_untrained_root(cuda):
+    """Training the root against the key CDF spreads the keys more evenly over the leaves
+    (the largest leaf shrinks against the untrained identity root); the mean windows of both
+    are recorded.  Both stay far below n."""
+    wl = W.normal_uniform_queries(1_000_000, 50_000, 0.001)
+    pts, qt, dt = to_dev(wl.points, cuda), to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
+    res = {}
+    for root in ("pwl", "mlp"):
+        for steps in (0, 300):
+            idx = sfc.sfc_build(pts, "z", bounds="learned", train_steps=steps, root=root)
+            sfc.query(idx, qt, dt)
+            st = sfc.sfc_model_stats(idx)
+            m = sfc.sfc_model_get(idx)
+            sizes = (m["end"].astype(np.int64) - m["first"].astype(np.int64))
+            res[(root, steps)] = (st["window_sum"] / st["endpoints"], int(sizes.max()))
+    print("normal points: (mean window, largest leaf) by (root, steps):", res)
+    assert res[("pwl", 300)][1] < res[("pwl", 0)][1], res
+    for v in res.values():
+        assert v[0] < wl.n / 100

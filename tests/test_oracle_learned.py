@@ -70,3 +70,43 @@ def test_error_window_contains_all():
     lo, hi = L.error_window(pos, pred)
     assert np.all(pos - pred >= lo) and np.all(pos - pred <= hi)
     assert lo == (pos - pred).min() and hi == (pos - pred).max()
+
+
+@pytest.mark.parametrize("K", [1, 4, 256])
+def test_pwl_gradient_vs_finite_differences(K):
+    rng = np.random.default_rng(K)
+    x = np.sort(rng.uniform(0, 1, 400))
+    y = np.linspace(0, 1, 400) ** 1.5
+    theta = L.pwl_init(K) + rng.normal(0, 0.01, K + 1)
+    loss, g = L.pwl_loss_grad(theta, x, y, K)
+    assert loss == pytest.approx(L.pwl_loss(theta, x, y, K), rel=1e-12)
+    eps = 1e-6
+    idx = range(K + 1) if K <= 8 else rng.choice(K + 1, 24, replace=False)
+    for i in idx:
+        tp = theta.copy(); tp[i] += eps
+        tm = theta.copy(); tm[i] -= eps
+        fd = (L.pwl_loss(tp, x, y, K) - L.pwl_loss(tm, x, y, K)) / (2 * eps)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-10)
+
+
+def test_pwl_init_is_identity_and_projection_monotone():
+    K = 256
+    x = np.linspace(0, 1, 10001)
+    np.testing.assert_allclose(L.pwl_forward(L.pwl_init(K), x, K), x, atol=1e-12)
+    rng = np.random.default_rng(3)
+    theta = L.pwl_project(L.pwl_init(K) + rng.normal(0, 0.05, K + 1))
+    assert np.all(np.diff(theta) >= 0)
+    assert np.all(np.diff(L.pwl_forward(theta, x, K)) >= 0)
+    # knots are interpolated exactly
+    np.testing.assert_allclose(L.pwl_forward(theta, np.arange(K) / K, K), theta[:K], rtol=1e-12)
+
+
+def test_pwl_least_squares_optimum_is_the_cdf_on_a_line():
+    """Data on the line y = 0.3 + 0.5 x: the least-squares heights are the line's values at
+    the knots (a closed form), and the analytic gradient vanishes there."""
+    K = 8
+    x = np.linspace(0, 1, 1001, endpoint=False)
+    y = 0.3 + 0.5 * x
+    h = 0.3 + 0.5 * np.arange(K + 1) / K
+    loss, g = L.pwl_loss_grad(h, x, y, K)
+    assert loss < 1e-28 and np.abs(g).max() < 1e-14

@@ -171,6 +171,12 @@ def density_matched_delta(rng, rho: np.ndarray, k_min=1.0, k_max=2000.0) -> np.n
     return np.clip(np.rint(d), 1, 2 ** 31 - 1).astype(np.int32)
 
 
+def normal_points(rng, n: int) -> np.ndarray:
+    """The paper's Normal distribution (Sec. 3, "Data"): centre at half the domain side,
+    standard deviation one eighth of it; rounded and clamped."""
+    return _clamp_round(rng.normal(SIDE / 2, SIDE / 8, size=(n, 2)))
+
+
 def queries_at_points(rng, pts: np.ndarray, m: int):
     idx = rng.integers(0, pts.shape[0], size=m)
     return pts[idx].copy(), idx
@@ -268,6 +274,17 @@ def dynamic_round_queries(wl: DynamicWorkload, r: int, live_xy: np.ndarray,
     qs, qi = queries_at_points(rd["query_rng"], live_xy, rd["m"])
     rho = wl.meta["mixture"].density(qs, live_cluster[qi])
     return qs, density_matched_delta(rd["delta_rng"], rho)
+
+
+def normal_uniform_queries(n: int, m: int, rel_side: float, seed: int = 6) -> Workload:
+    """The paper's static synthetic setting (Sec. 3.1): Normal points, uniform query centres,
+    and a disc whose diameter is rel_side times the domain side."""
+    rp, rq = _streams(seed, 2)
+    pts = normal_points(rp, n)
+    qs = uniform_points(rq, m)
+    delta = max(0, int(round(rel_side * SIDE / 2)))
+    return Workload("normal-uniform", pts, qs, np.full(m, delta, np.int32),
+                    {"seed": seed, "rel_side": rel_side, "delta": delta})
 
 
 WORKLOADS = {
