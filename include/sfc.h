@@ -238,6 +238,22 @@ sfc_status sfc_sort_pairs(const uint64_t* d_keys_in, const uint32_t* d_ids_in, u
 /* Exclusive prefix sum of n uint32 into uint64[n+1] (the last entry is the total). */
 sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
 
+/* sfc_exclusive_scan without any device allocation.  No counterpart in the paper: this is
+ * for callers that must not allocate device memory, such as code whose device memory is all
+ * owned by a caching pool of a host framework (an allocation from inside this library would
+ * go around the pool and can fail once the pool holds the memory), or a latency-bound loop
+ * that cannot take the implicit device synchronisation of cudaMalloc/cudaFree.  The call
+ * only enqueues a memset and one kernel on `stream`.
+ * Scratch: a fixed 131 KB array in device memory of every device that loads the library,
+ * held until the process exits; n may be at most 67,108,864 (16,384 tiles of 4,096),
+ * larger n returns SFC_ERR_CAPACITY and enqueues nothing.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current, so make
+ * that first call before capturing a stream into a CUDA graph.  All calls share the one
+ * array (it keeps the last call's words; each call clears what it uses first), so calls that
+ * can overlap on the GPU -- on different streams, or different host threads -- race and must
+ * be serialised by the caller.  Output: d_out uint64[n+1] as sfc_exclusive_scan. */
+sfc_status sfc_exclusive_scan_noalloc(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
+
 /* Ranges and bounds of a query batch (Alg. 1 lines 1-4): for each query i, up to four
  * merged key intervals of cells(Q) (d_lo/d_hi uint64[4m], unused slots lo = 1, hi = 0) and
  * their array bounds by the index's current bound search (d_begin/d_end uint32[4m]);

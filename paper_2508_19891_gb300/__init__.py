@@ -99,6 +99,7 @@ def lib():
             "sfc_decode": (ci, [P, u64, ci, P, P]),
             "sfc_sort_pairs": (ci, [P, P, u64, P, P, P]),
             "sfc_exclusive_scan": (ci, [P, u64, P, P]),
+            "sfc_exclusive_scan_noalloc": (ci, [P, u64, P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
             "sfc_query_stats": (ci, [P, P, P, P, P]),
@@ -466,6 +467,17 @@ def sfc_exclusive_scan(x: torch.Tensor, stream=None):
     x = x.contiguous()
     out = torch.empty(x.numel() + 1, dtype=torch.int64, device=x.device)
     _check(lib().sfc_exclusive_scan(_dptr(x), x.numel(), _dptr(out), _stream(stream)), "sfc_exclusive_scan")
+    return out
+
+
+def sfc_exclusive_scan_noalloc(x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Exclusive scan through the entry point that allocates no device memory (the output
+    buffer, if not given, is allocated here by torch, outside the library call)."""
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty(x.numel() + 1, dtype=torch.int64, device=x.device)
+    _check(lib().sfc_exclusive_scan_noalloc(_dptr(x), x.numel(), _dptr(out), _stream(stream)),
+           "sfc_exclusive_scan_noalloc")
     return out
 
 

@@ -8,6 +8,8 @@
 // its own inclusive prefix and writes its outputs.  A word packs a 2-bit flag with a
 // 62-bit sum.  The wait on a predecessor is bounded: past kSpinLimit reads it sets
 // SFC_DEV_TIMEOUT and continues with the partial sum.
+#include <mutex>
+
 #include "sfc_internal.cuh"
 
 namespace sfc {
@@ -144,4 +146,64 @@ sfc_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, Sca
     return launch_status();
 }
 
+// ------------------------------------------------------------------------------------
+// Scan without allocation (sfc_exclusive_scan_noalloc).
+//
+// For callers that must not allocate device memory.  Its look-back words live in a
+// file-scope device array of fixed size instead of a cudaMallocAsync buffer; host code
+// cannot use the array's name as a device address (it is a host-side stand-in), so the
+// address is taken once per device with cudaGetSymbolAddress while that device is current.
+// ------------------------------------------------------------------------------------
+constexpr uint64_t kNoAllocMaxTiles = 16384;                       // 131 KB of words
+constexpr uint64_t kNoAllocMaxItems = kNoAllocMaxTiles * kTile;     // 67,108,864 elements
+static __device__ __align__(256) uint64_t g_noalloc_scan_words[kNoAllocMaxTiles + 1];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_words[kMaxDevices] = {};
+
+// Device address of the array for the current device (looked up on first use).
+sfc_status noalloc_words(uint64_t** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SFC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_words[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scan_words);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SFC_ERR_CUDA;
+        }
+        g_noalloc_words[dev] = static_cast<uint64_t*>(p);
+    }
+    *out = g_noalloc_words[dev];
+    return SFC_OK;
+}
+
+}  // namespace
+
 }  // namespace sfc
+
+extern "C" sfc_status sfc_exclusive_scan_noalloc(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream)
+{
+    using namespace sfc;
+    if (!d_out || (n && !d_in)) return SFC_ERR_INVALID;
+    if (n > kNoAllocMaxItems) return SFC_ERR_CAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t* words = nullptr;
+    SFC_TRY(noalloc_words(&words));
+    if (n == 0) {
+        SFC_CUDA_TRY(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
+        return SFC_OK;
+    }
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    // the tile counter and the look-back words of this call must start at zero
+    SFC_CUDA_TRY(cudaMemsetAsync(words, 0, (tiles + 1) * sizeof(uint64_t), st));
+    const int vec = ((((uintptr_t)d_in) & 15) == 0) && ((((uintptr_t)d_out) & 15) == 0);
+    scan_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(d_in, n, d_out, words, nullptr, vec);
+    count_launch();
+    return launch_status();
+}
