@@ -40,8 +40,8 @@ WORKLOAD = "mixed-1e7"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
@@ -91,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -331,7 +331,35 @@ def extras(sfc, torch, pts, q, d, total, n, m, flush):
         res["device_status"] = st[0]
         ix.close()
         out[curve] = res
+    out["update"] = update_round(sfc, torch, pts, flush)
     return out
+
+
+def update_round(sfc, torch, pts, flush):
+    """One dynamic round shaped like the dynamic workload (delete 5% of the live ids, insert
+    10% new points from the same distribution), on the learned Z index: batch sort, merge,
+    and the model refit."""
+    n = pts.shape[0]
+    k_del, k_ins = n // 20, n // 10
+    rng = np.random.default_rng(99)
+    dels = torch.from_numpy(rng.choice(n, k_del, replace=False).astype(np.int32)).to(pts.device)
+    ins = pts[torch.from_numpy(rng.integers(0, n, k_ins)).to(pts.device)].contiguous()
+    times = []
+    for rep in range(3):
+        ix = sfc.sfc_build(pts, "z", bounds="learned")
+        torch.cuda.synchronize()
+        flush.fill_(rep)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sfc.sfc_update(ix, ins, dels)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        ix.close()
+    ms = min(times)
+    return {"deletes": k_del, "inserts": k_ins, "ms": ms,
+            "updated_pts_per_s": (k_del + k_ins) / (ms / 1e3),
+            "note": "includes the host validation sync and the learned-model refit"}
 
 
 def e2e(sfc, torch, wl, total, bounds, args):

@@ -222,8 +222,8 @@ void sfc_default_options(sfc_options* opt)
     if (!opt) return;
     opt->bounds = SFC_BOUNDS_BINARY;
     opt->leaves = 4096;
-    opt->train_steps = 300;
-    opt->train_samples = 65536;
+    opt->train_steps = 100;
+    opt->train_samples = 16384;
     opt->learning_rate = 0.02f;
     opt->chunk = 0;
     opt->mask_budget_mb = 4096;
@@ -261,6 +261,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     sfc_status s = ensure_status_buf(idx, st);
     if (s == SFC_OK) s = build_from_device(idx, d_points, st);
     if (s == SFC_OK && o.bounds == SFC_BOUNDS_LEARNED) {
+        ProfScope ps(idx, "train", st);
         s = train_model(idx, st);
         if (s == SFC_OK) idx->bounds = SFC_BOUNDS_LEARNED;
     }

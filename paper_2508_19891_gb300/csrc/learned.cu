@@ -37,7 +37,7 @@ constexpr int kMaxNP = kNPPwl > kNPMlp ? kNPPwl : kNPMlp;
 constexpr int kTrainThreads = 256;
 constexpr int kTrainBlocks = 64;
 constexpr int kPartial = kMaxNP + 1;      // per-block partial: gradient entries + loss
-constexpr double kFix = 1125899906842624.0;   // 2^50: fixed-point scale of the knot sums
+constexpr float kFix32 = 536870912.0f;   // 2^29: fixed-point scale of the knot sums
 
 __host__ __device__ constexpr int num_params(int kind) { return kind == kRootPwl ? kNPPwl : kNPMlp; }
 
@@ -186,27 +186,16 @@ __device__ bool last_block(unsigned* counter)
     return s_last;
 }
 
-// ---- MLP root: one step (update != 0) or only the loss and gradient ----
-__global__ void __launch_bounds__(kTrainThreads)
-train_mlp_step_kernel(const float* __restrict__ x, const float* __restrict__ y, uint32_t N, TrainState* ts,
-                      float* partial /* [gridDim.x][kPartial] */, unsigned* counter, float lr, int update,
-                      int leaves)
+// Per-thread gradient (g[0..3H]) and loss (g[3H+1]) of the MLP root over samples i0,
+// i0 + stride, ...
+__device__ void mlp_accumulate(const float* __restrict__ x, const float* __restrict__ y, uint32_t N, uint32_t i0,
+                               uint32_t stride, const float* sA, const float* sB, const float* sb, float sc,
+                               float (&g)[kNPMlp + 1])
 {
-    __shared__ float sA[kHidden], sB[kHidden], sb[kHidden], sc;
-    __shared__ float sred[kTrainThreads / 32][kNPMlp + 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < kHidden) {
-        sA[tid] = ts->root.A[tid];
-        sB[tid] = ts->root.B[tid];
-        sb[tid] = ts->root.b[tid];
-    }
-    if (tid == 0) sc = ts->root.c;
-    __syncthreads();
     const float invN = 1.0f / (float)N;
-    float g[kNPMlp + 1];
 #pragma unroll
     for (int j = 0; j <= kNPMlp; ++j) g[j] = 0.0f;
-    for (uint32_t s = blockIdx.x * kTrainThreads + tid; s < N; s += gridDim.x * kTrainThreads) {
+    for (uint32_t s = i0; s < N; s += stride) {
         const float xi = x[s], yi = y[s];
         float h[kHidden];
         float f = sc;
@@ -229,6 +218,26 @@ train_mlp_step_kernel(const float* __restrict__ x, const float* __restrict__ y, 
             g[kHidden + k] += ra * sk * sB[k] * xi;        // dL/dbeta_k
         }
     }
+}
+
+// ---- MLP root: one step (update != 0) or only the loss and gradient ----
+__global__ void __launch_bounds__(kTrainThreads)
+train_mlp_step_kernel(const float* __restrict__ x, const float* __restrict__ y, uint32_t N, TrainState* ts,
+                      float* partial /* [gridDim.x][kPartial] */, unsigned* counter, float lr, int update,
+                      int leaves)
+{
+    __shared__ float sA[kHidden], sB[kHidden], sb[kHidden], sc;
+    __shared__ float sred[kTrainThreads / 32][kNPMlp + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kHidden) {
+        sA[tid] = ts->root.A[tid];
+        sB[tid] = ts->root.B[tid];
+        sb[tid] = ts->root.b[tid];
+    }
+    if (tid == 0) sc = ts->root.c;
+    __syncthreads();
+    float g[kNPMlp + 1];
+    mlp_accumulate(x, y, N, blockIdx.x * kTrainThreads + tid, gridDim.x * kTrainThreads, sA, sB, sb, sc, g);
 #pragma unroll
     for (int j = 0; j <= kNPMlp; ++j) {
         const float w = warp_sum(g[j]);
@@ -255,6 +264,67 @@ train_mlp_step_kernel(const float* __restrict__ x, const float* __restrict__ y, 
     if (tid == 0) *counter = 0;
 }
 
+// Accumulates dL/dh of samples i0, i0 + stride, ... into sg[0..K] as 32-bit fixed point
+// (scale 2^29: every term is at most 2/N in magnitude and a knot's sum at most 4, so the
+// integer sums are exact and independent of the order of the atomics) and returns the thread's
+// share of the loss.  The loop bound is uniform across each warp; when all lanes of a warp fall
+// in one knot interval (the common case: samples are sorted) the warp adds its sums with one
+// atomic per knot.
+__device__ float pwl_accumulate(const float* __restrict__ x, const float* __restrict__ y, uint32_t N, uint32_t i0,
+                                uint32_t stride, const float* sh, int* sg)
+{
+    const float invN = 1.0f / (float)N;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wbase = i0 - lane;
+    float loss = 0.0f;
+    for (uint32_t base = wbase; base < N; base += stride) {
+        const uint32_t s = base + lane;
+        const bool ok = s < N;
+        int k = 0, a = 0, b = 0;
+        if (ok) {
+            const float xs = x[s] * (float)kKnots;
+            k = (int)xs;
+            k = k < 0 ? 0 : (k > kKnots - 1 ? kKnots - 1 : k);
+            const float t = xs - (float)k;
+            const float f = fmaf(sh[k + 1] - sh[k], t, sh[k]);
+            const float res = f - y[s];
+            const float r = 2.0f * res * invN;
+            a = __float2int_rn(r * (1.0f - t) * kFix32);
+            b = __float2int_rn(r * t * kFix32);
+            loss = fmaf(res * res, invN, loss);
+        }
+        const int k0 = __shfl_sync(0xffffffffu, k, 0);
+        if (__all_sync(0xffffffffu, !ok || k == k0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&sg[k0], a);
+                atomicAdd(&sg[k0 + 1], b);
+            }
+        } else if (ok) {
+            atomicAdd(&sg[k], a);
+            atomicAdd(&sg[k + 1], b);
+        }
+    }
+    return loss;
+}
+
+// Block-wide float sum in a fixed order (every thread calls it; result valid in all threads).
+__device__ float block_sum_f(float v, float* sh32)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh32[warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh32[w];
+    return t;
+}
+
 // ---- piecewise-linear root: one step (update != 0) or only the loss and gradient ----
 // With s = xK, k = floor(s), t = s - k: f = h_k + (h_{k+1} - h_k) t, so dL/dh_k gets
 // r (1 - t) and dL/dh_{k+1} gets r t (r = 2 (f - y) / N).  After the Adam update the heights
@@ -266,36 +336,31 @@ train_pwl_step_kernel(const float* __restrict__ x, const float* __restrict__ y, 
                       int update, int leaves)
 {
     __shared__ float sh[kKnots + 1];
-    __shared__ unsigned long long sg[kKnots + 2];   // knot gradients, then the loss
+    __shared__ int sg[kKnots + 1];
+    __shared__ float s32[kTrainThreads / 32];
     const int tid = threadIdx.x;
-    for (int j = tid; j <= kKnots; j += kTrainThreads) sh[j] = ts->root.h[j];
-    for (int j = tid; j <= kKnots + 1; j += kTrainThreads) sg[j] = 0ull;
-    __syncthreads();
-    const float invN = 1.0f / (float)N;
-    for (uint32_t s = blockIdx.x * kTrainThreads + tid; s < N; s += gridDim.x * kTrainThreads) {
-        const float xs = x[s] * (float)kKnots;
-        int k = (int)xs;
-        k = k < 0 ? 0 : (k > kKnots - 1 ? kKnots - 1 : k);
-        const float t = xs - (float)k;
-        const float f = fmaf(sh[k + 1] - sh[k], t, sh[k]);
-        const float res = f - y[s];
-        const float r = 2.0f * res * invN;
-        atomicAdd(&sg[k], (unsigned long long)__double2ll_rn((double)(r * (1.0f - t)) * kFix));
-        atomicAdd(&sg[k + 1], (unsigned long long)__double2ll_rn((double)(r * t) * kFix));
-        atomicAdd(&sg[kKnots + 1], (unsigned long long)__double2ll_rn((double)(res * res * invN) * kFix));
+    for (int j = tid; j <= kKnots; j += kTrainThreads) {
+        sh[j] = ts->root.h[j];
+        sg[j] = 0;
     }
     __syncthreads();
-    for (int j = tid; j <= kKnots + 1; j += kTrainThreads) partial[blockIdx.x * kPartial + j] = (long long)sg[j];
+    const float l = pwl_accumulate(x, y, N, blockIdx.x * kTrainThreads + tid, gridDim.x * kTrainThreads, sh, sg);
+    const float bl = block_sum_f(l, s32);
+    __syncthreads();
+    for (int j = tid; j <= kKnots; j += kTrainThreads) partial[blockIdx.x * kPartial + j] = (long long)sg[j];
+    if (tid == 0) partial[blockIdx.x * kPartial + kKnots + 1] = (long long)__float_as_int(bl);
     if (!last_block(counter)) return;
-    __shared__ double sgh[kKnots + 2];
-    for (int j = tid; j <= kKnots + 1; j += kTrainThreads) {
+    for (int j = tid; j <= kKnots; j += kTrainThreads) {
         long long acc = 0;
         for (unsigned b = 0; b < gridDim.x; ++b) acc += *((volatile long long*)partial + b * kPartial + j);
-        sgh[j] = (double)acc / kFix;
+        ts->grad[j] = (float)acc / kFix32;
     }
-    __syncthreads();
-    for (int j = tid; j <= kKnots; j += kTrainThreads) ts->grad[j] = (float)sgh[j];
-    if (tid == 0) ts->loss = (float)sgh[kKnots + 1];
+    if (tid == 0) {
+        float acc = 0.0f;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            acc += __int_as_float((int)*((volatile long long*)partial + b * kPartial + kKnots + 1));
+        ts->loss = acc;
+    }
     __syncthreads();
     if (update) {
         adam_update(ts, lr);
@@ -305,6 +370,117 @@ train_pwl_step_kernel(const float* __restrict__ x, const float* __restrict__ y, 
         derive_root(ts, leaves);
     }
     if (tid == 0) *counter = 0;
+}
+
+// ---- the whole training run in one block: per step the same gradient as the step
+// kernels, then Adam with a linearly decaying step size (and the monotone projection for the
+// piecewise-linear root).  One launch instead of one per step. ----
+// Threads of the training-loop block: the piecewise-linear root keeps few registers per
+// thread, the MLP root holds a 50-entry gradient per thread.
+template <int KIND>
+struct LoopThreads { static constexpr int value = KIND == kRootPwl ? 1024 : 512; };
+
+template <int KIND>
+__global__ void __launch_bounds__(LoopThreads<KIND>::value)
+train_loop_kernel(const float* __restrict__ x, const float* __restrict__ y, uint32_t N, TrainState* ts, int steps,
+                  float lr0, int leaves)
+{
+    constexpr int kLoopThreads = LoopThreads<KIND>::value;
+    // optimiser state stays in shared memory for the whole run
+    __shared__ float th[kMaxNP], mo[kMaxNP], ve[kMaxNP], gr[kMaxNP];
+    __shared__ float sh[kKnots + 1];
+    __shared__ int sg[kKnots + 1];
+    __shared__ float s32[kLoopThreads / 32];
+    __shared__ float sred[kLoopThreads / 32][kNPMlp + 1];
+    __shared__ float sA[kHidden], sB[kHidden], sb[kHidden], sc;
+    __shared__ float s_loss;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr bool pwl = KIND == kRootPwl;
+    const int np = ts->np;
+    for (int j = tid; j < kMaxNP; j += kLoopThreads) {
+        th[j] = ts->theta[j];
+        mo[j] = ts->m[j];
+        ve[j] = ts->v[j];
+    }
+    const int t0 = ts->t;
+    __syncthreads();
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int step = 0; step < steps; ++step) {
+        const float lr = lr0 * (float)(steps - step) / (float)steps;
+        // current root in shared memory
+        if constexpr (pwl) {
+            for (int j = tid; j <= kKnots; j += kLoopThreads) {
+                sh[j] = th[j];
+                sg[j] = 0;
+            }
+        } else {
+            if (tid < kHidden) {
+                sA[tid] = expf(th[tid]);
+                sB[tid] = expf(th[kHidden + tid]);
+                sb[tid] = th[2 * kHidden + tid];
+            }
+            if (tid == 0) sc = th[3 * kHidden];
+        }
+        __syncthreads();
+        if constexpr (pwl) {
+            const float l = pwl_accumulate(x, y, N, tid, kLoopThreads, sh, sg);
+            const float bl = block_sum_f(l, s32);
+            __syncthreads();
+            for (int j = tid; j <= kKnots; j += kLoopThreads) gr[j] = (float)sg[j] / kFix32;
+            if (tid == 0) s_loss = bl;
+        } else {
+            float g[kNPMlp + 1];
+            mlp_accumulate(x, y, N, tid, kLoopThreads, sA, sB, sb, sc, g);
+            (void)s32;
+#pragma unroll
+            for (int j = 0; j <= kNPMlp; ++j) {
+                const float w = warp_sum(g[j]);
+                if (lane == 0) sred[warp][j] = w;
+            }
+            __syncthreads();
+            for (int j = tid; j <= kNPMlp; j += kLoopThreads) {
+                float acc = 0.0f;
+                for (int w = 0; w < kLoopThreads / 32; ++w) acc += sred[w][j];
+                if (j == kNPMlp) s_loss = acc;
+                else gr[j] = acc;
+            }
+        }
+        __syncthreads();
+        // Adam, bias-corrected at step t
+        const int t = t0 + step + 1;
+        const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+        for (int j = tid; j < np; j += kLoopThreads) {
+            const float gj = gr[j];
+            const float mj = b1 * mo[j] + (1.0f - b1) * gj;
+            const float vj = b2 * ve[j] + (1.0f - b2) * gj * gj;
+            mo[j] = mj;
+            ve[j] = vj;
+            th[j] -= lr * (mj / c1) / (sqrtf(vj / c2) + eps);
+        }
+        __syncthreads();
+        if (pwl) {   // running maximum (Hillis-Steele scan) keeps the knot heights monotone
+            for (int o = 1; o <= kKnots; o <<= 1) {
+                float v = 0.0f;
+                const bool has = tid <= kKnots && tid >= o;
+                if (has) v = th[tid - o];
+                __syncthreads();
+                if (has) th[tid] = fmaxf(th[tid], v);
+                __syncthreads();
+            }
+        }
+    }
+    for (int j = tid; j < kMaxNP; j += kLoopThreads) {
+        ts->theta[j] = th[j];
+        ts->m[j] = mo[j];
+        ts->v[j] = ve[j];
+        ts->grad[j] = gr[j];
+    }
+    if (tid == 0) {
+        ts->t = t0 + steps;
+        ts->loss = s_loss;
+    }
+    __syncthreads();
+    derive_root(ts, leaves);
 }
 
 // Adam update alone on given state (sfc_model_adam_step).
@@ -401,48 +577,34 @@ __global__ void __launch_bounds__(1024) leaf_fix_kernel(const LeafTmp* tmp, int 
     }
 }
 
-__device__ __forceinline__ double block_sum_d(double v, double* sh)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    return t;
-}
-
-// One block per leaf: v = position - first against u = key - base over [first, end).
+// One block per leaf: v = position - first against u = key - base over [first, end), in
+// fp32 with centred second pass and fixed-order tree reductions.  The line only places the
+// search window; the window itself is measured exactly afterwards (leaf_err_kernel).
 __global__ void __launch_bounds__(256) leaf_fit_kernel(const uint64_t* __restrict__ keys, LeafParams* leaf)
 {
-    __shared__ double sh[8];
+    __shared__ float sh[8];
     LeafParams lp = leaf[blockIdx.x];
     const uint32_t cnt = lp.end - lp.first;
     if (cnt < 2) {
         if (threadIdx.x == 0) { leaf[blockIdx.x].slope = 0.0f; leaf[blockIdx.x].icpt = 0.0f; }
         return;
     }
-    double su = 0.0, sv = 0.0;
+    float su = 0.0f;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) su += __ull2float_rn(keys[lp.first + i] - lp.base);
+    const float mu = block_sum_f(su, sh) / (float)cnt;
+    const float mv = 0.5f * (float)(cnt - 1);   // mean of 0 .. cnt - 1
+    float sxy = 0.0f, sxx = 0.0f;
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        su += (double)(keys[lp.first + i] - lp.base);
-        sv += (double)i;
+        const float du = __ull2float_rn(keys[lp.first + i] - lp.base) - mu;
+        sxy = fmaf(du, (float)i - mv, sxy);
+        sxx = fmaf(du, du, sxx);
     }
-    const double mu = block_sum_d(su, sh) / cnt;
-    const double mv = block_sum_d(sv, sh) / cnt;
-    double sxy = 0.0, sxx = 0.0;
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const double du = (double)(keys[lp.first + i] - lp.base) - mu;
-        sxy += du * ((double)i - mv);
-        sxx += du * du;
-    }
-    sxy = block_sum_d(sxy, sh);
-    sxx = block_sum_d(sxx, sh);
+    sxy = block_sum_f(sxy, sh);
+    sxx = block_sum_f(sxx, sh);
     if (threadIdx.x == 0) {
-        const double slope = sxx > 0.0 ? sxy / sxx : 0.0;
-        leaf[blockIdx.x].slope = (float)slope;
-        leaf[blockIdx.x].icpt = (float)(mv - slope * mu);
+        const float slope = sxx > 0.0f ? sxy / sxx : 0.0f;
+        leaf[blockIdx.x].slope = slope;
+        leaf[blockIdx.x].icpt = mv - slope * mu;
     }
 }
 
@@ -573,17 +735,11 @@ static sfc_status train_root(sfc_index* idx, int steps, bool warm, cudaStream_t 
         // heights live on [0, 1] where a leaf is 1/4096 wide: the piecewise-linear root
         // refines with a twentieth of the MLP's step size
         const float lr0 = idx->opt.learning_rate * (kind == kRootPwl ? 0.05f : 1.0f);
-        for (int s = 0; s < steps; ++s) {
-            // step size decays linearly to zero over the run
-            const float lr = lr0 * (float)(steps - s) / (float)steps;
-            if (kind == kRootPwl)
-                train_pwl_step_kernel<<<kTrainBlocks, kTrainThreads, 0, st>>>(
-                    x, y, N, ts, M.partial.as<long long>(), counter, lr, 1, leaves);
-            else
-                train_mlp_step_kernel<<<kTrainBlocks, kTrainThreads, 0, st>>>(
-                    x, y, N, ts, M.partial.as<float>(), counter, lr, 1, leaves);
-        }
-        count_launch((uint64_t)steps);
+        if (kind == kRootPwl)
+            train_loop_kernel<kRootPwl><<<1, LoopThreads<kRootPwl>::value, 0, st>>>(x, y, N, ts, steps, lr0, leaves);
+        else
+            train_loop_kernel<kRootMlp><<<1, LoopThreads<kRootMlp>::value, 0, st>>>(x, y, N, ts, steps, lr0, leaves);
+        count_launch();
     }
     SFC_TRY(launch_status());
     SFC_TRY(fit_leaves(idx, st));
