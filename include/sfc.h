@@ -102,6 +102,42 @@ sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, 
 /* Frees the index and everything it owns (stream-ordered on the stream of the last call). */
 void sfc_destroy(sfc_index* idx);
 
+/* Rebuilds the index in place over n new points (device), with the index's curve and
+ * options: keys, sort, coordinates, the id table (ids restart at 0..n-1) and, if the index
+ * uses learned bounds, a fresh model fit.  Reuses the index's buffers (they only grow), so
+ * after sfc_reserve it allocates nothing.  Errors as sfc_build. */
+sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void* stream);
+
+/* Sizes every buffer of the index for rebuilds of up to n_max points and query batches of up
+ * to m_max queries, so that later sfc_rebuild / sfc_query_* calls allocate nothing (needed
+ * before capturing them in a CUDA graph). */
+sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* CUDA graphs: the whole pipeline captured once, replayed with one launch.            */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct sfc_graph sfc_graph;   /* opaque; owned by the library */
+
+#define SFC_GRAPH_REBUILD 0x1u   /* sfc_rebuild(d_points, n) (+ model fit if learned) */
+#define SFC_GRAPH_QUERY   0x2u   /* sfc_query_batch(d_q, d_delta, m, offsets, ids, capacity) */
+
+/* Captures the selected steps, with these exact pointers and sizes, into a CUDA graph (on a
+ * private stream; `stream` orders the set-up work) and instantiates it.  Replays read the
+ * buffers' contents at replay time, so new points or queries written into the same buffers
+ * are answered by the next sfc_graph_launch.  Calls sfc_reserve(n, m) first.  The index must
+ * outlive the graph and must not be used by other calls while a replay runs. */
+sfc_status sfc_graph_capture(sfc_index* idx, unsigned flags, const int32_t* d_points, uint64_t n,
+                             const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                             uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t ids_capacity,
+                             sfc_graph** out, void* stream);
+
+/* Replays a captured pipeline on `stream` (one graph launch). */
+sfc_status sfc_graph_launch(sfc_graph* g, void* stream);
+
+/* Frees the graph (not the index). */
+void sfc_graph_destroy(sfc_graph* g);
+
 /* ---------------------------------------------------------------------------------- */
 /* Queries (Alg. 1 for a batch).                                                        */
 /* ---------------------------------------------------------------------------------- */

@@ -102,6 +102,11 @@ def lib():
             "sfc_exclusive_scan_noalloc": (ci, [P, u64, P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
+            "sfc_rebuild": (ci, [P, P, u64, P]),
+            "sfc_reserve": (ci, [P, u64, u64, P]),
+            "sfc_graph_capture": (ci, [P, ctypes.c_uint, P, u64, P, P, u64, P, P, u64, PP, P]),
+            "sfc_graph_launch": (ci, [P, P]),
+            "sfc_graph_destroy": (None, [P]),
             "sfc_query_stats": (ci, [P, P, P, P, P]),
             "sfc_profile_enable": (ci, [P, ci]),
             "sfc_profile_read": (ci, [P, P, ci, P, ci, P]),
@@ -251,6 +256,55 @@ def sfc_build_host(points: np.ndarray, curve="z", options: sfc_options | None = 
 
 def sfc_destroy(index: Index):
     index.close()
+
+
+def sfc_rebuild(index: Index, points: torch.Tensor, stream=None):
+    points = _pts(points)
+    _check(lib().sfc_rebuild(index.handle, _dptr(points), points.shape[0], _stream(stream)), "sfc_rebuild")
+
+
+def sfc_reserve(index: Index, n_max: int, m_max: int, stream=None):
+    _check(lib().sfc_reserve(index.handle, int(n_max), int(m_max), _stream(stream)), "sfc_reserve")
+
+
+SFC_GRAPH_REBUILD = 0x1
+SFC_GRAPH_QUERY = 0x2
+
+
+class Graph:
+    """A captured pipeline (sfc_graph); keeps the tensors it reads and writes alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().sfc_graph_launch(self._h, _stream(stream)), "sfc_graph_launch")
+
+    def close(self):
+        if self._h:
+            lib().sfc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfc_graph_capture(index: Index, points: torch.Tensor | None, q: torch.Tensor | None,
+                      delta: torch.Tensor | None, out_offsets: torch.Tensor | None,
+                      out_ids: torch.Tensor | None, capacity: int | None = None, stream=None) -> Graph:
+    flags = (SFC_GRAPH_REBUILD if points is not None else 0) | (SFC_GRAPH_QUERY if q is not None else 0)
+    n = points.shape[0] if points is not None else 0
+    m = q.shape[0] if q is not None else 0
+    cap = (out_ids.numel() if out_ids is not None else 0) if capacity is None else int(capacity)
+    h = ctypes.c_void_p()
+    _check(lib().sfc_graph_capture(index.handle, flags, _dptr(points), n, _dptr(q), _dptr(delta), m,
+                                   _dptr(out_offsets), _dptr(out_ids) if (out_ids is not None and out_ids.numel()) else None,
+                                   cap, ctypes.byref(h), _stream(stream)), "sfc_graph_capture")
+    return Graph(h, (index, points, q, delta, out_offsets, out_ids))
 
 
 def sfc_query_count(index: Index, q: torch.Tensor, delta: torch.Tensor,

@@ -2,6 +2,7 @@
 // workspaces, and the order of kernel launches for each call.  No computation of the method
 // happens here; every step runs in the kernels of keygen.cu, radix.cu, scan.cu, query.cu,
 // learned.cu and update.cu.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -299,6 +300,103 @@ void sfc_destroy(sfc_index* idx)
     idx->prof.recs.clear();
     release_index(idx, st);
     delete idx;
+}
+
+sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void* stream)
+{
+    if (!idx || n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    idx->last_stream = st;
+    idx->n = n;
+    idx->qws.pending.valid = false;
+    SFC_TRY(ensure_status_buf(idx, st));
+    // every issued id is live again
+    if (idx->alive.ptr) SFC_CUDA_TRY(cudaMemsetAsync(idx->alive.ptr, 0xff, idx->alive.bytes, st));
+    SFC_TRY(build_from_device(idx, d_points, st));
+    if (idx->opt.bounds == SFC_BOUNDS_LEARNED) {
+        ProfScope ps(idx, "train", st);
+        SFC_TRY(train_model(idx, st));
+    }
+    return SFC_OK;
+}
+
+sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* stream)
+{
+    if (!idx || n_max >= 0xffffffffull) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    SFC_TRY(ensure_status_buf(idx, st));
+    const uint64_t n1 = n_max ? n_max : 1;
+    SFC_TRY(idx->keys.ensure(n1 * sizeof(uint64_t), st));
+    SFC_TRY(idx->ids.ensure(n1 * sizeof(uint32_t), st));
+    SFC_TRY(idx->xy.ensure(n1 * sizeof(int2), st));
+    SFC_TRY(idx->xy_by_id.ensure(n1 * sizeof(int2), st));
+    SFC_TRY(ensure_alive_bits(idx, n1, st));
+    SFC_TRY(reserve_sort(idx->sort_ws, n1, st));
+    SFC_TRY(ensure_query_ws(idx, m_max, st));
+    SFC_TRY(reserve_scan(idx->scan_ws, std::max<uint64_t>(m_max, n1) + 1, st));
+    if (idx->opt.bounds == SFC_BOUNDS_LEARNED) SFC_TRY(reserve_model(idx, n1, st));
+    return SFC_OK;
+}
+
+}  // extern "C"
+
+struct sfc_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+sfc_status sfc_graph_capture(sfc_index* idx, unsigned flags, const int32_t* d_points, uint64_t n,
+                             const int32_t* d_q, const int32_t* d_delta, uint64_t m, uint64_t* d_out_offsets,
+                             uint32_t* d_out_ids, uint64_t ids_capacity, sfc_graph** out, void* stream)
+{
+    if (!idx || !out || !flags || (flags & ~(SFC_GRAPH_REBUILD | SFC_GRAPH_QUERY))) return SFC_ERR_INVALID;
+    *out = nullptr;
+    const bool rb = flags & SFC_GRAPH_REBUILD, qb = flags & SFC_GRAPH_QUERY;
+    if (rb && (n >= 0xffffffffull || (n && !d_points))) return SFC_ERR_INVALID;
+    if (qb && (!d_out_offsets || (m && (!d_q || !d_delta)) || (ids_capacity && !d_out_ids))) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    SFC_TRY(sfc_reserve(idx, rb ? n : idx->n, qb ? m : 0, stream));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));   // set-up done before capture starts
+    cudaStream_t cs = nullptr;
+    SFC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    sfc_graph* g = new (std::nothrow) sfc_graph();
+    if (!g) { cudaStreamDestroy(cs); return SFC_ERR_OOM; }
+    sfc_status s = SFC_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = SFC_ERR_CUDA;
+    if (s == SFC_OK && rb) s = sfc_rebuild(idx, d_points, n, cs);
+    if (s == SFC_OK && qb) s = sfc_query_batch(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, ids_capacity, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (s == SFC_OK && ce != cudaSuccess) s = SFC_ERR_CUDA;
+    if (s == SFC_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) s = SFC_ERR_CUDA;
+    g->graph = graph;
+    cudaStreamDestroy(cs);
+    idx->last_stream = st;
+    if (s != SFC_OK) {
+        cudaGetLastError();
+        sfc_graph_destroy(g);
+        return s;
+    }
+    *out = g;
+    return SFC_OK;
+}
+
+sfc_status sfc_graph_launch(sfc_graph* g, void* stream)
+{
+    if (!g || !g->exec) return SFC_ERR_INVALID;
+    SFC_CUDA_TRY(cudaGraphLaunch(g->exec, as_stream(stream)));
+    count_launch();
+    return SFC_OK;
+}
+
+void sfc_graph_destroy(sfc_graph* g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
 }
 
 sfc_status sfc_query_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,

@@ -87,6 +87,7 @@ sfc_status ensure_alive_bits(sfc_index* idx, uint64_t ids, cudaStream_t st);
 void release_index(sfc_index* idx, cudaStream_t st);
 sfc_status train_model(sfc_index* idx, cudaStream_t st);
 sfc_status fit_leaves(sfc_index* idx, cudaStream_t st);
+sfc_status reserve_model(sfc_index* idx, uint64_t n, cudaStream_t st);
 sfc_status refit_model(sfc_index* idx, int steps, cudaStream_t st);
 sfc_status apply_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins, const uint32_t* d_del,
                         uint64_t k_del, uint32_t* h_first, cudaStream_t st);
@@ -98,6 +99,8 @@ public:
     ProfScope(sfc_index* idx, const char* name, cudaStream_t st) : idx_(idx), st_(st)
     {
         if (!idx || !idx->prof.on) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
         rec_.name = name;
         if (cudaEventCreate(&rec_.a) != cudaSuccess) return;
         if (cudaEventCreate(&rec_.b) != cudaSuccess) { cudaEventDestroy(rec_.a); return; }

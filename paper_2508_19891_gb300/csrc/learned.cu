@@ -699,6 +699,25 @@ sfc_status fit_leaves(sfc_index* idx, cudaStream_t st)
     return launch_status();
 }
 
+static uint32_t sample_count(const sfc_index* idx, uint64_t n)
+{
+    return (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>((uint64_t)idx->opt.train_samples, std::max<uint64_t>(n, 2)));
+}
+
+sfc_status reserve_model(sfc_index* idx, uint64_t n, cudaStream_t st)
+{
+    ModelState& M = idx->model;
+    const int leaves = idx->opt.leaves;
+    const uint32_t N = sample_count(idx, n);
+    SFC_TRY(M.state.ensure(sizeof(TrainState), st));
+    SFC_TRY(M.samples.ensure((size_t)N * 2 * sizeof(float), st));
+    SFC_TRY(M.partial.ensure((size_t)kTrainBlocks * kPartial * sizeof(long long) + 256, st));
+    SFC_TRY(M.tmp.ensure((size_t)leaves * sizeof(LeafTmp), st));
+    SFC_TRY(M.leaves.ensure((size_t)leaves * sizeof(LeafParams), st));
+    SFC_TRY(M.route.ensure(std::max<uint64_t>(n, 1) * sizeof(uint32_t), st));
+    return SFC_OK;
+}
+
 // Trains the root from its initial parameters (warm: continue from the current ones for
 // `steps` more steps), then fits the leaves.
 static sfc_status train_root(sfc_index* idx, int steps, bool warm, cudaStream_t st)
@@ -707,8 +726,7 @@ static sfc_status train_root(sfc_index* idx, int steps, bool warm, cudaStream_t 
     const int leaves = idx->opt.leaves;
     const int kind = idx->opt.root == SFC_ROOT_MLP ? kRootMlp : kRootPwl;
     const uint64_t n = idx->n;
-    const uint32_t N = (uint32_t)std::max<uint64_t>(
-        2, std::min<uint64_t>((uint64_t)idx->opt.train_samples, std::max<uint64_t>(n, 2)));
+    const uint32_t N = sample_count(idx, n);
     const bool fresh = !M.state.ptr;
     SFC_TRY(M.state.ensure(sizeof(TrainState), st));
     SFC_TRY(M.samples.ensure((size_t)N * 2 * sizeof(float), st));

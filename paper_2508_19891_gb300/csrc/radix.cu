@@ -19,8 +19,9 @@
 //                    random gather xy[id] by a streaming write.
 //
 // Look-back words are tagged with a per-pass epoch, so stale words from earlier passes or
-// sorts read as "not ready" and the buffer never needs clearing.  Every wait is bounded
-// (SFC_DEV_TIMEOUT).
+// sorts read as "not ready" and the buffer never needs clearing.  The epoch counter lives in
+// device memory and is advanced by plan_kernel, so a sort replayed from a CUDA graph still
+// gets fresh epochs.  Every wait is bounded (SFC_DEV_TIMEOUT).
 #include "sfc_internal.cuh"
 
 namespace sfc {
@@ -48,6 +49,7 @@ struct Small {
     uint32_t offs[kPasses][kRadix];
     PassPlan plan[kPasses];
     uint32_t tile_ctr[kPasses];
+    uint32_t epoch_base;   // epoch of pass 0 of this sort (pass p uses epoch_base + p)
 };
 
 constexpr uint64_t kFlagAgg = 1ull << 32;
@@ -113,8 +115,15 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(SortSource src, uint64_t
 }
 
 // One block of 256 threads (thread = digit).
-__global__ void __launch_bounds__(kRadix) plan_kernel(Small* sm, uint64_t n)
+__global__ void __launch_bounds__(kRadix) plan_kernel(Small* sm, uint64_t n, uint32_t* epoch_ctr)
 {
+    if (threadIdx.x == 0) {
+        // 30-bit epochs, never 0 (the value of a cleared word); wraps after 2^27 sorts
+        uint32_t e = *epoch_ctr;
+        if (e + kPasses >= (1u << 30)) e = 0;
+        sm->epoch_base = e + 1;
+        *epoch_ctr = e + kPasses;
+    }
     __shared__ uint32_t s_const[kPasses];
     __shared__ uint32_t s_w[kRadix / 32];
     const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
@@ -163,7 +172,6 @@ struct PassArgs {
     uint64_t n;
     uint32_t* status;
     int pass;
-    uint32_t epoch;
 };
 
 constexpr size_t kSortSmem = sizeof(uint64_t) * kTile + sizeof(uint32_t) * kTile +
@@ -175,6 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(PassArgs a)
 {
     const PassPlan pl = a.sm->plan[a.pass];
     if (!pl.active) return;
+    const uint32_t epoch = a.sm->epoch_base + (uint32_t)a.pass;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
@@ -248,9 +257,9 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(PassArgs a)
     }
     uint64_t* lbw = a.lookback + tile * kRadix + tid;
     if (tile == 0) {
-        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagPrefix, a.epoch));
+        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagPrefix, epoch));
     } else {
-        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagAgg, a.epoch));
+        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagAgg, epoch));
     }
     // tile-local exclusive scan over digits
     {
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(PassArgs a)
             uint64_t w = *reinterpret_cast<volatile uint64_t*>(a.lookback + (uint64_t)t * kRadix + tid);
             uint32_t ep = (uint32_t)(w >> 34);
             uint32_t fl = (uint32_t)(w >> 32) & 3u;
-            if (ep != a.epoch || fl == 0) {
+            if (ep != epoch || fl == 0) {
                 if (++spins > kSpinLimit) { set_status(a.status, SFC_DEV_TIMEOUT); break; }
                 continue;
             }
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(PassArgs a)
             --t;
         }
         atomicExch(reinterpret_cast<unsigned long long*>(lbw),
-                   lb_word(excl + tcount, kFlagPrefix, a.epoch));
+                   lb_word(excl + tcount, kFlagPrefix, epoch));
     }
     s_gbase[tid] = a.sm->offs[a.pass][tid] + excl;
     __syncthreads();
@@ -333,6 +342,28 @@ void release_sort_ws(SortWorkspace& ws, cudaStream_t st)
     }
     ws.lookback.release(st);
     ws.small.release(st);
+    ws.epoch_dev.release(st);
+}
+
+sfc_status reserve_sort(SortWorkspace& ws, uint64_t n, cudaStream_t st)
+{
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    for (int i = 0; i < 2; ++i) {
+        SFC_TRY(ws.tmp_keys[i].ensure(n * sizeof(uint64_t), st));
+        SFC_TRY(ws.tmp_vals[i].ensure(n * sizeof(uint32_t), st));
+    }
+    const size_t lb_bytes = tiles * kRadix * sizeof(uint64_t);
+    if (!ws.epoch_dev.ptr) {
+        SFC_TRY(ws.epoch_dev.ensure(sizeof(uint32_t), st));
+        SFC_CUDA_TRY(cudaMemsetAsync(ws.epoch_dev.ptr, 0, sizeof(uint32_t), st));
+    }
+    if (lb_bytes > ws.lookback.bytes) {
+        // new words start cleared; older epochs stay distinct from future ones
+        SFC_TRY(ws.lookback.ensure(lb_bytes, st));
+        SFC_CUDA_TRY(cudaMemsetAsync(ws.lookback.ptr, 0, ws.lookback.bytes, st));
+    }
+    SFC_TRY(ws.small.ensure(sizeof(Small), st));
+    return SFC_OK;
 }
 
 sfc_status radix_sort(const SortSource& src, uint64_t n, const SortDest& dst, SortWorkspace& ws,
@@ -342,17 +373,7 @@ sfc_status radix_sort(const SortSource& src, uint64_t n, const SortDest& dst, So
     if (n >= 0xffffffffull) return SFC_ERR_INVALID;
     if (src.points && dst.curve != src.curve) return SFC_ERR_INVALID;
     const uint64_t tiles = (n + kTile - 1) / kTile;
-    for (int i = 0; i < 2; ++i) {
-        SFC_TRY(ws.tmp_keys[i].ensure(n * sizeof(uint64_t), st));
-        SFC_TRY(ws.tmp_vals[i].ensure(n * sizeof(uint32_t), st));
-    }
-    const size_t lb_bytes = tiles * kRadix * sizeof(uint64_t);
-    if (lb_bytes > ws.lookback.bytes) {
-        SFC_TRY(ws.lookback.ensure(lb_bytes, st));
-        SFC_CUDA_TRY(cudaMemsetAsync(ws.lookback.ptr, 0, ws.lookback.bytes, st));
-        ws.epoch = 0;
-    }
-    SFC_TRY(ws.small.ensure(sizeof(Small), st));
+    SFC_TRY(reserve_sort(ws, n, st));
     Small* sm = ws.small.as<Small>();
     SFC_CUDA_TRY(cudaMemsetAsync(sm, 0, sizeof(Small), st));
 
@@ -365,7 +386,7 @@ sfc_status radix_sort(const SortSource& src, uint64_t n, const SortDest& dst, So
         hist_kernel<SFC_CURVE_Z><<<hgrid, kThreads, 0, st>>>(src, n, sm, status);
     count_launch();
     SFC_TRY(launch_status());
-    plan_kernel<<<1, kRadix, 0, st>>>(sm, n);
+    plan_kernel<<<1, kRadix, 0, st>>>(sm, n, ws.epoch_dev.as<uint32_t>());
     count_launch();
     SFC_TRY(launch_status());
 
@@ -392,10 +413,7 @@ sfc_status radix_sort(const SortSource& src, uint64_t n, const SortDest& dst, So
     a.n = n;
     a.status = status;
     for (int p = 0; p < kPasses; ++p) {
-        ws.epoch = (ws.epoch + 1) & ((1u << 30) - 1);
-        if (ws.epoch == 0) ws.epoch = 1;
         a.pass = p;
-        a.epoch = ws.epoch;
         if (curve == SFC_CURVE_HILBERT)
             onesweep_kernel<SFC_CURVE_HILBERT><<<(unsigned)tiles, kThreads, kSortSmem, st>>>(a);
         else

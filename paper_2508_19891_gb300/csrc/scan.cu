@@ -129,6 +129,12 @@ scan_kernel(const uint32_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ 
 
 }  // namespace
 
+sfc_status reserve_scan(ScanWorkspace& ws, uint64_t n, cudaStream_t st)
+{
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    return ws.flags.ensure((tiles + 1) * sizeof(uint64_t), st);
+}
+
 sfc_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, ScanWorkspace& ws,
                               uint32_t* status, cudaStream_t st)
 {
