@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
+    ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5"], default="mixed-1e7",
+                    help="the headline is mixed-1e7; the others are supplementary measurements")
+    ap.add_argument("--reorder", type=int, choices=[0, 1, 2], default=None,
+                    help="query processing order (0 input, 1 curve, 2 automatic)")
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -137,7 +141,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    wl = workloads.mixed_1e7(scale=args.scale, seed=instance_seed(rank))
+    wl = make_workload(args, rank)
     n, m = wl.n, wl.m
     bounds = args.bounds or ("learned" if learned_available(sfc) else "binary")
     pts = torch.from_numpy(wl.points).to(dev)
@@ -145,6 +149,8 @@ def run_ours(args, rank, world, local):
     d = torch.from_numpy(wl.delta).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     opts = dict(bounds=bounds, profile=1)
+    if args.reorder is not None:
+        opts["reorder_queries"] = args.reorder
 
     # size the output once: the total is the same for every step
     idx = sfc.sfc_build(pts, "z", **opts)
@@ -219,7 +225,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "curve": "z", "bounds": bounds,
+        "config": {"workload": args.workload, "n": n, "m": m, "curve": "z", "bounds": bounds,
+                   "reorder_queries": opts.get("reorder_queries", 2),
                    "seed": instance_seed(rank), "l2": "flushed between timed steps (256 MB write)",
                    "step": "build (keys+sort+decode) + learned-model fit if enabled + query batch"},
         "roofline": {"kernel": "count_kernel", "bound": "hbm", "achieved": achieved,
@@ -250,6 +257,14 @@ def run_ours(args, rank, world, local):
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def make_workload(args, rank):
+    if args.workload == "mixed-1e8":
+        return workloads.mixed_1e8(scale=args.scale, seed=4 + 7919 * rank)
+    if args.workload == "uniform-1e5":
+        return workloads.uniform_1e5(scale=args.scale, seed=1 + 7919 * rank)
+    return workloads.mixed_1e7(scale=args.scale, seed=instance_seed(rank))
 
 
 def learned_available(sfc) -> bool:

@@ -72,7 +72,10 @@ typedef struct {
     float learning_rate;    /* learned model: Adam step size (default 0.02) */
     int chunk;              /* scan chunk in points (0 = autotuned/default 1024) */
     int mask_budget_mb;     /* device memory for hit masks of the two-pass scan (default 1024) */
-    int reorder_queries;    /* 1 = process queries in curve order for cache reuse (default 1) */
+    int reorder_queries;    /* order in which queries are processed (outputs are unaffected):
+                               0 input order, 1 curve order of the centres (queries that scan
+                               overlapping ranges run together and share L2), 2 curve order once
+                               the coordinates outgrow L2, n >= 2^24 (default 2) */
     int profile;            /* 1 = record per-step CUDA events from the start (sfc_profile_read) */
     sfc_root root;          /* learned model: root kind (default SFC_ROOT_PWL) */
 } sfc_options;

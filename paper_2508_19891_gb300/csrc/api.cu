@@ -122,6 +122,14 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
     SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
+    if (idx->opt.reorder_queries != 0) {
+        SFC_TRY(w.qkeys.ensure(m * sizeof(uint64_t), st));
+        SFC_TRY(w.qkeys_sorted.ensure(m * sizeof(uint64_t), st));
+        SFC_TRY(w.perm.ensure(m * sizeof(uint32_t), st));
+        SFC_TRY(w.nch_sorted.ensure(m * sizeof(uint32_t), st));
+        SFC_TRY(w.wbase.ensure((m + 1) * sizeof(uint64_t), st));
+        SFC_TRY(reserve_sort(idx->sort_ws, std::max<uint64_t>(m, 1), st));
+    }
     const uint64_t budget = (uint64_t)idx->opt.mask_budget_mb << 20;
     uint64_t want = m * 4096ull + (1ull << 20);
     if (want > budget) want = budget;
@@ -138,13 +146,22 @@ const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
     return &v;
 }
 
+// Curve-order processing pays off once the coordinates no longer fit in L2 (n >= 2^24, i.e.
+// 128 MB of coordinates); option 1 forces it, 0 disables it.
+bool use_curve_order(const sfc_index* idx, uint64_t m)
+{
+    if (m < 2 || idx->opt.reorder_queries == 0) return false;
+    if (idx->opt.reorder_queries == 1) return true;
+    return idx->n >= (1ull << 24);
+}
+
 sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
                     uint64_t* d_out_offsets, cudaStream_t st)
 {
     SFC_TRY(ensure_status_buf(idx, st));
     if (m == 0) {
         SFC_CUDA_TRY(cudaMemsetAsync(d_out_offsets, 0, sizeof(uint64_t), st));
-        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0};
+        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0, false};
         return SFC_OK;
     }
     SFC_TRY(ensure_query_ws(idx, m, st));
@@ -167,6 +184,20 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     SFC_CUDA_TRY(cudaMemsetAsync(a.counts, 0, m * sizeof(uint32_t), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, 4 * sizeof(unsigned long long), st));
     LearnedModelView lv;
+    const bool ordered = use_curve_order(idx, m);
+    if (ordered) {
+        // processing order: queries sorted by the curve key of their centre, so that queries
+        // scanning overlapping ranges run close together and share the cache
+        ProfScope ps(idx, "order", st);
+        SFC_TRY(launch_query_keys(d_q, m, idx->curve, w.qkeys.as<uint64_t>(), st));
+        SortSource src;
+        src.keys = w.qkeys.as<uint64_t>();
+        SortDest dst;
+        dst.keys = w.qkeys_sorted.as<uint64_t>();
+        dst.vals = w.perm.as<uint32_t>();
+        dst.curve = idx->curve;
+        SFC_TRY(radix_sort(src, m, dst, idx->sort_ws, a.status, st));
+    }
     {
         ProfScope ps(idx, "plan", st);
         SFC_TRY(launch_plan(a, model_view(idx, lv), st));
@@ -174,6 +205,13 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     {
         ProfScope ps(idx, "scan", st);
         SFC_TRY(exclusive_scan_u32(a.nchunks, m, a.chunk_base, idx->scan_ws, a.status, st));
+        if (ordered) {
+            SFC_TRY(launch_gather_u32(a.nchunks, w.perm.as<uint32_t>(), m, w.nch_sorted.as<uint32_t>(), st));
+            SFC_TRY(exclusive_scan_u32(w.nch_sorted.as<uint32_t>(), m, w.wbase.as<uint64_t>(), idx->scan_ws,
+                                       a.status, st));
+            a.perm = w.perm.as<uint32_t>();
+            a.wbase = w.wbase.as<uint64_t>();
+        }
     }
     {
         ProfScope ps(idx, "count", st);
@@ -183,7 +221,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         ProfScope ps(idx, "scan", st);
         SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
     }
-    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk};
+    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered};
     return SFC_OK;
 }
 
@@ -209,6 +247,10 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.work_ctr = w.ctr.as<unsigned long long>();
     a.out_offsets = const_cast<uint64_t*>(d_out_offsets);
     a.out_ids = d_out_ids;
+    if (w.pending.ordered) {
+        a.perm = w.perm.as<uint32_t>();
+        a.wbase = w.wbase.as<uint64_t>();
+    }
     a.ids_capacity = d_out_ids ? cap : 0;
     ProfScope ps(idx, "write", st);
     return launch_write(a, st);
@@ -228,7 +270,7 @@ void sfc_default_options(sfc_options* opt)
     opt->learning_rate = 0.02f;
     opt->chunk = 0;
     opt->mask_budget_mb = 4096;
-    opt->reorder_queries = 1;
+    opt->reorder_queries = 2;
     opt->profile = 0;
     opt->root = SFC_ROOT_PWL;
 }
@@ -244,7 +286,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     sfc_default_options(&o);
     if (opt) o = *opt;
     if (o.leaves < 1 || o.leaves > (1 << 20) || o.mask_budget_mb < 1 || o.train_samples < 2 ||
-        o.train_steps < 0 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
+        o.train_steps < 0 || o.reorder_queries < 0 || o.reorder_queries > 2 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
         (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED) ||
         (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP))
         return SFC_ERR_INVALID;

@@ -14,11 +14,13 @@ struct PendingCount {       // plan kept between sfc_query_count and sfc_query_w
     uint64_t m;
     const uint64_t* offsets;
     uint32_t chunk;
+    bool ordered;           // queries processed in curve order (perm / wbase valid)
 };
 
 struct QueryWs {
     DevBuf ranges, nchunks, chunk_base, counts, masks, ctr;
-    PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0};
+    DevBuf qkeys, qkeys_sorted, perm, nch_sorted, wbase;   // curve-order processing
+    PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false};
 };
 
 struct HostStage {          // device staging of sfc_query_batch_host

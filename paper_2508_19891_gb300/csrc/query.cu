@@ -383,7 +383,9 @@ template <int WPL>
 __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 {
     const unsigned lane = lane_id();
-    const uint64_t G = a.chunk_base[a.m];
+    // work items are chunks in processing order: wbase (curve order) or chunk_base (input order)
+    const uint64_t* wb = a.wbase ? a.wbase : a.chunk_base;
+    const uint64_t G = wb[a.m];
     const uint32_t W = a.chunk >> 5;   // mask words per chunk
     while (true) {
         uint64_t g0 = 0;
@@ -391,11 +393,13 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
         g0 = __shfl_sync(0xffffffffu, g0, 0);
         if (g0 >= G) break;
         const uint64_t g1 = min(G, g0 + a.batch);
-        uint64_t q = owner_query(a.chunk_base, a.m, g0);
-        for (uint64_t g = g0; g < g1; ++g) {
-            while (__ldg(a.chunk_base + q + 1) <= g) ++q;
+        uint64_t r = owner_query(wb, a.m, g0);
+        for (uint64_t w = g0; w < g1; ++w) {
+            while (__ldg(wb + r + 1) <= w) ++r;
+            const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
             const QView v = load_query(a, q);
-            const uint32_t j = (uint32_t)(g - __ldg(a.chunk_base + q));
+            const uint32_t j = (uint32_t)(w - __ldg(wb + r));
+            const uint64_t g = a.perm ? __ldg(a.chunk_base + q) + j : w;   // mask slot
             const uint32_t s0 = j * a.chunk;
             const uint32_t s1 = min(v.S, s0 + a.chunk);
             uint32_t words[WPL];
@@ -433,7 +437,8 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
         q0 = __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= a.m) break;
         const uint64_t q1 = min(a.m, q0 + a.qbatch);
-        for (uint64_t q = q0; q < q1; ++q) {
+        for (uint64_t r = q0; r < q1; ++r) {
+            const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
             const uint32_t k = __ldg(a.counts + q);
             if (k == 0) continue;
             const QView v = load_query(a, q);
@@ -526,6 +531,23 @@ __global__ void __launch_bounds__(kThreads) ranges_kernel(QueryArgs a, Bounds bo
     if (out_cnt) out_cnt[i] = (uint32_t)R.cnt;
 }
 
+__global__ void query_keys_kernel(const int32_t* __restrict__ q, uint64_t m, int curve, uint64_t* keys)
+{
+    __shared__ HilbertTables tb;
+    if (curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int2 c = reinterpret_cast<const int2*>(q)[i];
+        keys[i] = point_in_domain(c.x, c.y) ? curve_key(curve, &tb, (uint32_t)c.x, (uint32_t)c.y) : ~0ull;
+    }
+}
+
+__global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ perm, uint64_t m,
+                                  uint32_t* out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = src[perm[i]];
+}
+
 int persistent_grid(const void* fn)
 {
     int per_sm = 0;
@@ -560,6 +582,29 @@ sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStrea
     } else {
         plan_kernel<BinaryBounds><<<g, kThreads, 0, st>>>(a, BinaryBounds{});
     }
+    count_launch();
+    return launch_status();
+}
+
+static unsigned flat_grid(uint64_t m)
+{
+    uint64_t g = (m + kThreads - 1) / kThreads;
+    const uint64_t cap = (uint64_t)num_sms() * 16;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st)
+{
+    if (m == 0) return SFC_OK;
+    query_keys_kernel<<<flat_grid(m), kThreads, 0, st>>>(q, m, curve, keys);
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_gather_u32(const uint32_t* src, const uint32_t* perm, uint64_t m, uint32_t* out, cudaStream_t st)
+{
+    if (m == 0) return SFC_OK;
+    gather_u32_kernel<<<flat_grid(m), kThreads, 0, st>>>(src, perm, m, out);
     count_launch();
     return launch_status();
 }

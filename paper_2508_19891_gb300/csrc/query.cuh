@@ -29,6 +29,9 @@ struct QueryArgs {
     uint64_t ids_capacity;
     uint32_t* status;
     unsigned long long* scanned;   // sum of S_q over the batch (statistics)
+    // optional processing order: queries handed out in curve order of their centres
+    const uint32_t* perm;        // [m] query index at each processing rank (NULL: identity)
+    const uint64_t* wbase;       // [m + 1] chunk bases in processing order (NULL: chunk_base)
 };
 
 struct LearnedModelView {
@@ -39,6 +42,10 @@ struct LearnedModelView {
 
 sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st);
 sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
+// curve key of each query centre (invalid centres sort last) with the query index as value
+sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);
+// out[r] = nchunks[perm[r]]
+sfc_status launch_gather_u32(const uint32_t* src, const uint32_t* perm, uint64_t m, uint32_t* out, cudaStream_t st);
 sfc_status launch_write(const QueryArgs& a, cudaStream_t st);
 sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_t* lo, uint64_t* hi,
                          uint32_t* b, uint32_t* e, uint32_t* cnt, cudaStream_t st);

@@ -149,3 +149,17 @@ def test_host_buffer_api(cuda, curve):
 def test_roads_scaled(cuda):
     wl = W.roads_3e7(scale=0.005)
     assert_same(wl.points, wl.queries, wl.delta, "h", cuda)
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
+def test_processing_order_does_not_change_results(cuda, curve, reorder):
+    """Queries handed out in curve order of their centres (option 1) or input order (0) give
+    identical offsets and id lists; invalid centres sort last."""
+    wl = W.mixed_1e7(scale=0.01)
+    qs = wl.queries.copy()
+    d = wl.delta.copy()
+    qs[::97] = [-5, 3]          # a few invalid centres
+    for bounds in ("binary", "learned"):
+        idx, st = assert_same(wl.points, qs, d, curve, cuda, reorder_queries=reorder, bounds=bounds)
+        assert st[1] & ~sfc.SFC_DEV_BAD_QUERY == 0
