@@ -305,45 +305,70 @@ __device__ __forceinline__ bool is_hit(const QView& v, int2 p)
     return s <= v.d2;
 }
 
+// Stores ballot words w0..w3 (points s0 + 32 * (it + u) ...) in lanes it % 32 .. it % 32 + 3 of
+// slot it / 32.
+template <int WPL>
+__device__ __forceinline__ void keep_words(uint32_t (&words)[WPL], uint32_t it, uint32_t w0, uint32_t w1,
+                                           uint32_t w2, uint32_t w3)
+{
+    const uint32_t d = lane_id() - (it & 31);
+    if (d < 4) {
+        const uint32_t w = d == 0 ? w0 : d == 1 ? w1 : d == 2 ? w2 : w3;
+        const uint32_t slot = it >> 5;
+#pragma unroll
+        for (int s = 0; s < WPL; ++s)
+            if (slot == (uint32_t)s) words[s] = w;
+    }
+}
+
 // Filters points [s0, s1) of the query's concatenated intervals; returns the hit count and
-// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.  Each
-// lane advances its array position by 32 per word and looks the interval up again only when
-// it crosses into the next one.
+// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.  Points go in
+// groups of 4 x 32: when the whole group lies inside the chunk and no lane crosses the end of
+// its interval (one vote), the group runs without per-point guards; otherwise each point is
+// checked and the lane looks its interval up again when it crosses into the next one.
 template <int WPL>
 __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, uint32_t s0,
                                                  uint32_t s1, uint32_t (&words)[WPL])
 {
-    const unsigned lane = lane_id();
 #pragma unroll
     for (int s = 0; s < WPL; ++s) words[s] = 0;
-    uint32_t cnt = 0;
     const uint32_t nit = (s1 - s0 + 31) >> 5;
     const int2* __restrict__ xy = a.xy;
-    uint32_t f = s0 + lane;
+    uint32_t f = s0 + lane_id();
     uint32_t shift, end;
     interval_of(v, f, shift, end);
-    for (uint32_t it = 0; it < nit; it += 4) {
-        int2 p[4];
-        bool val[4];
+    for (uint32_t it = 0; it < nit; it += 4, f += 128) {
+        const bool full = s0 + (it + 4) * 32 <= s1;     // warp-uniform
+        if (full && __all_sync(0xffffffffu, f + 96 < end)) {
+            const int2* p = xy + (f + shift);
+            const int2 p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
+            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit(v, p0));
+            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit(v, p1));
+            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit(v, p2));
+            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit(v, p3));
+            keep_words<WPL>(words, it, w0, w1, w2, w3);
+        } else {
+            int2 p[4];
+            bool val[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t fu = f + 32u * u;
-            val[u] = fu < s1;
-            if (fu >= end) interval_of(v, fu, shift, end);
-            p[u] = val[u] ? __ldg(xy + (fu + shift)) : make_int2(0, 0);
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t fu = f + 32u * u;
+                val[u] = fu < s1;
+                if (fu >= end) interval_of(v, fu, shift, end);
+                p[u] = val[u] ? __ldg(xy + (fu + shift)) : make_int2(0, 0);
+            }
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit(v, p[u]));
+            keep_words<WPL>(words, it, w[0], w[1], w[2], w[3]);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t w = __ballot_sync(0xffffffffu, val[u] && is_hit(v, p[u]));
-            cnt += __popc(w);
-            const uint32_t wi = it + u;
-#pragma unroll
-            for (int s = 0; s < WPL; ++s)
-                if (wi == (uint32_t)(s * 32) + lane) words[s] = w;
-        }
-        f += 128;
     }
-    return cnt;
+    uint32_t c = 0;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) c += __popc(words[s]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
@@ -473,14 +498,22 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                     uint32_t slot = incl - pc;
                     uint32_t bits = wl;
                     const uint32_t fbase = s0 + ((uint32_t)(s * 32) + lane) * 32u;
-                    while (bits) {
-                        const int b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        buf[slot++] = map_pos(v, fbase + (uint32_t)b);
+                    if (bits) {
+                        // one interval lookup per word; a word that crosses an interval end
+                        // maps each bit separately
+                        uint32_t shift, end;
+                        interval_of(v, fbase, shift, end);
+                        const bool one = fbase + 31 < end;
+                        while (bits) {
+                            const uint32_t f = fbase + (uint32_t)(__ffs(bits) - 1);
+                            bits &= bits - 1;
+                            buf[slot++] = one ? f + shift : map_pos(v, f);
+                        }
                     }
                     __syncwarp();
                     // coalesced gather of the ids and write of the output
                     const uint64_t dst0 = off + rank;
+#pragma unroll 4
                     for (uint32_t t = lane; t < K; t += 32) {
                         const uint64_t dst = dst0 + t;
                         const uint32_t id = __ldg(a.ids + buf[t]);

@@ -179,7 +179,7 @@ constexpr size_t kSortSmem = sizeof(uint64_t) * kTile + sizeof(uint32_t) * kTile
                              sizeof(HilbertTables);
 
 template <int CURVE>
-__global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(PassArgs a)
+__global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(PassArgs a)
 {
     const PassPlan pl = a.sm->plan[a.pass];
     if (!pl.active) return;
