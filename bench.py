@@ -192,13 +192,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     local_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pg.barrier()
-    else:
-        total_ms = local_ms
+    total_ms = max_over_ranks(local_ms, pg, dev)
     # per-step device times of the library's steps (events on the launching stream)
     agg = {}
     for ix in profs:
@@ -213,7 +207,7 @@ def run_ours(args, rank, world, local):
         raise RuntimeError(f"device status {status} bits {bits:#x}")
 
     ms_per_step = total_ms / args.steps
-    value = world * m / (ms_per_step / 1e3)
+    value = job_throughput(m, world, ms_per_step)
     hbm_peak, peak_kind = peaks()
     # dominant kernel: the count pass (one launch per step)
     count_runs, count_ms = agg.get("count", (0, float("nan")))
@@ -257,6 +251,24 @@ def run_ours(args, rank, world, local):
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def max_over_ranks(local_ms: float, pg=None, device=None) -> float:
+    """Timed-region length of the slowest rank (the only cross-rank exchange: timing, not
+    data).  With no process group it is the local time."""
+    if pg is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.barrier()
+    return float(t.item())
+
+
+def job_throughput(m_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Queries answered per second by the whole job: every rank answers its own m queries per
+    step (weak scaling), and the step time is the slowest rank's."""
+    return world * m_per_rank / (ms_per_step / 1e3)
 
 
 def make_workload(args, rank):
