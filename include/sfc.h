@@ -178,6 +178,16 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
  * allocate nothing (needed before capturing them in a CUDA graph). */
 sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream);
 
+/* Autotuner: times the count pass (plan + scan + count) of this query batch for chunk sizes
+ * {256, 512, 1024, 2048, 4096} points (threads-per-query granularity of the scan), then the
+ * number of chunks taken per work-queue grab {1, 2, 4, 8, 16}, then the queries per write-pass
+ * grab {1, 2, 4, 8, 16}, and keeps the fastest in the index (results do not depend on them).
+ * The choice is cached per (device, curve, log2 n, log2 m) for later indexes; force != 0
+ * re-measures.  Writes the choice to *h_chunk, *h_batch, *h_qbatch (any may be NULL).
+ * Synchronises `stream`; allocates a temporary output buffer. */
+sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m, int force,
+                        int* h_chunk, int* h_batch, int* h_qbatch, void* stream);
+
 /* Chooses the bound search of later queries.  SFC_BOUNDS_LEARNED requires a trained model
  * (sfc_train_model or opt->bounds at build), else SFC_ERR_STATE. */
 sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);

@@ -102,6 +102,7 @@ def lib():
             "sfc_exclusive_scan_noalloc": (ci, [P, u64, P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
+            "sfc_autotune": (ci, [P, P, P, u64, ci, P, P, P, P]),
             "sfc_rebuild": (ci, [P, P, u64, P]),
             "sfc_reserve": (ci, [P, u64, u64, P]),
             "sfc_graph_capture": (ci, [P, ctypes.c_uint, P, u64, P, P, u64, P, P, u64, PP, P]),
@@ -364,6 +365,15 @@ def sfc_query_batch_host(index: Index, q: np.ndarray, delta: np.ndarray, capacit
                                     _hptr(out_ids), int(capacity), _stream(stream))
     _check(st, "sfc_query_batch_host")
     return out_offsets, out_ids[:int(out_offsets[m])]
+
+
+def sfc_autotune(index: Index, q: torch.Tensor, delta: torch.Tensor, force: bool = False, stream=None) -> dict:
+    q = _pts(q)
+    delta = delta.contiguous()
+    c, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sfc_autotune(index.handle, _dptr(q), _dptr(delta), q.shape[0], int(bool(force)), ctypes.byref(c),
+                              ctypes.byref(b), ctypes.byref(w), _stream(stream)), "sfc_autotune")
+    return {"chunk": c.value, "batch": b.value, "qbatch": w.value}
 
 
 def sfc_reserve_queries(index: Index, m: int, stream=None):

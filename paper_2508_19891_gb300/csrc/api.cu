@@ -252,6 +252,8 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         a.wbase = w.wbase.as<uint64_t>();
     }
     a.ids_capacity = d_out_ids ? cap : 0;
+    // the write pass's own work counter starts at zero (a repeated write stays correct)
+    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + 1, 0, sizeof(unsigned long long), st));
     ProfScope ps(idx, "write", st);
     return launch_write(a, st);
 }
@@ -464,6 +466,137 @@ sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_
 {
     SFC_TRY(sfc_query_count(idx, d_q, d_delta, m, d_out_offsets, stream));
     return sfc_query_write(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, ids_capacity, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct TuneKey {
+    int device, curve, lgn, lgm, bounds;
+    bool operator==(const TuneKey& o) const
+    {
+        return device == o.device && curve == o.curve && lgn == o.lgn && lgm == o.lgm && bounds == o.bounds;
+    }
+};
+
+struct TuneVal {
+    uint32_t chunk, batch, qbatch;
+};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+int lg2(uint64_t v)
+{
+    int l = 0;
+    while (v > 1) { v >>= 1; ++l; }
+    return l;
+}
+
+// Device time of fn() on st with CUDA events (best of reps).
+template <class F>
+sfc_status time_on(cudaStream_t st, int reps, float* best, F fn)
+{
+    cudaEvent_t a, b;
+    SFC_CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return SFC_ERR_CUDA; }
+    *best = 1e30f;
+    sfc_status s = SFC_OK;
+    for (int r = 0; r < reps && s == SFC_OK; ++r) {
+        cudaEventRecord(a, st);
+        s = fn();
+        cudaEventRecord(b, st);
+        if (s == SFC_OK && cudaEventSynchronize(b) == cudaSuccess) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < *best) *best = ms;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m, int force,
+                        int* h_chunk, int* h_batch, int* h_qbatch, void* stream)
+{
+    if (!idx || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    const TuneKey key{idx->device, (int)idx->curve, lg2(idx->n + 1), lg2(m + 1), (int)idx->bounds};
+    bool cached = false;
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                idx->chunk = kv.second.chunk;
+                idx->batch = kv.second.batch;
+                idx->qbatch = kv.second.qbatch;
+                cached = true;
+            }
+    }
+    if (!cached && m > 0) {
+        const bool prof = idx->prof.on;
+        idx->prof.on = false;
+        DevBuf off;
+        sfc_status s = off.ensure((m + 1) * sizeof(uint64_t), st);
+        auto count = [&]() { return do_count(idx, d_q, d_delta, m, off.as<uint64_t>(), st); };
+        float best = 1e30f, t = 0.0f;
+        uint32_t bc = idx->chunk, bb = idx->batch, bq = idx->qbatch;
+        for (uint32_t c : {256u, 512u, 1024u, 2048u, 4096u}) {
+            if (s != SFC_OK) break;
+            idx->chunk = c;
+            idx->batch = 4;
+            s = time_on(st, 2, &t, count);
+            if (t < best) { best = t; bc = c; }
+        }
+        idx->chunk = bc;
+        best = 1e30f;
+        for (uint32_t b : {1u, 2u, 4u, 8u, 16u}) {
+            if (s != SFC_OK) break;
+            idx->batch = b;
+            s = time_on(st, 2, &t, count);
+            if (t < best) { best = t; bb = b; }
+        }
+        idx->batch = bb;
+        // write pass: one count with the chosen settings, then time the writes
+        uint64_t total = 0;
+        if (s == SFC_OK) s = count();
+        if (s == SFC_OK && cudaMemcpyAsync(&total, off.as<uint64_t>() + m, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess) s = SFC_ERR_CUDA;
+        if (s == SFC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SFC_ERR_CUDA;
+        DevBuf ids;
+        if (s == SFC_OK) s = ids.ensure(std::max<uint64_t>(total, 1) * sizeof(uint32_t), st);
+        best = 1e30f;
+        for (uint32_t qb : {1u, 2u, 4u, 8u, 16u}) {
+            if (s != SFC_OK) break;
+            idx->qbatch = qb;
+            s = time_on(st, 2, &t, [&]() {
+                idx->qws.pending.valid = true;   // the plan of the last count is still in place
+                return do_write(idx, d_q, d_delta, m, off.as<uint64_t>(), ids.as<uint32_t>(), total, st);
+            });
+            if (t < best) { best = t; bq = qb; }
+        }
+        idx->qbatch = bq;
+        idx->qws.pending.valid = false;
+        ids.release(st);
+        off.release(st);
+        idx->prof.on = prof;
+        cudaStreamSynchronize(st);
+        if (s != SFC_OK) return s;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        bool found = false;
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) { kv.second = TuneVal{bc, bb, bq}; found = true; }
+        if (!found) g_tune_cache.push_back({key, TuneVal{bc, bb, bq}});
+    }
+    if (h_chunk) *h_chunk = (int)idx->chunk;
+    if (h_batch) *h_batch = (int)idx->batch;
+    if (h_qbatch) *h_qbatch = (int)idx->qbatch;
+    return SFC_OK;
 }
 
 sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta, uint64_t m,

@@ -163,3 +163,19 @@ def test_processing_order_does_not_change_results(cuda, curve, reorder):
     for bounds in ("binary", "learned"):
         idx, st = assert_same(wl.points, qs, d, curve, cuda, reorder_queries=reorder, bounds=bounds)
         assert st[1] & ~sfc.SFC_DEV_BAD_QUERY == 0
+
+
+def test_autotune(cuda):
+    """The autotuner picks among the documented candidates, caches its choice per shape, and
+    the answers after tuning still equal the oracle's."""
+    wl = W.mixed_1e7(scale=0.02)
+    q, d = to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
+    idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned")
+    choice = sfc.sfc_autotune(idx, q, d, force=True)
+    assert choice["chunk"] in (256, 512, 1024, 2048, 4096)
+    assert choice["batch"] in (1, 2, 4, 8, 16) and choice["qbatch"] in (1, 2, 4, 8, 16)
+    idx2 = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned")
+    assert sfc.sfc_autotune(idx2, q, d) == choice          # served from the cache
+    off, ids = sfc.query(idx2, q, d)
+    roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta)
+    assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
