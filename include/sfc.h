@@ -71,7 +71,8 @@ typedef struct {
     int train_samples;      /* learned model: keys sampled for root training (default 16384) */
     float learning_rate;    /* learned model: Adam step size (default 0.02) */
     int chunk;              /* scan chunk in points (0 = autotuned/default 1024) */
-    int mask_budget_mb;     /* device memory for hit masks of the two-pass scan (default 1024) */
+    int mask_budget_mb;     /* cap on the hit-mask buffer of the two-pass scan, which is sized
+                               1 KB per query (default cap 4096 MB) */
     int reorder_queries;    /* order in which queries are processed (outputs are unaffected):
                                0 input order, 1 curve order of the centres (queries that scan
                                overlapping ranges run together and share L2), 2 curve order once
@@ -168,8 +169,9 @@ sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_
                            uint64_t ids_capacity, void* stream);
 
 /* Whole query batch with host buffers: copies h_q/h_delta in, runs the batch, copies
- * h_out_offsets (uint64[m+1]) and the ids back.  Synchronises `stream`.  If the total
- * exceeds ids_capacity, only h_out_offsets is written and SFC_ERR_CAPACITY is returned. */
+ * h_out_offsets (uint64[m+1]) and the ids back (staged in device memory; page-locked host
+ * buffers copy fastest).  Synchronises `stream`.  If the total exceeds ids_capacity, only h_out_offsets is
+ * written and SFC_ERR_CAPACITY is returned. */
 sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta,
                                 uint64_t m, uint64_t* h_out_offsets, uint32_t* h_out_ids,
                                 uint64_t ids_capacity, void* stream);

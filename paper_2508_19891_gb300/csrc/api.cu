@@ -29,9 +29,28 @@ int num_sms()
     return cached[dev];
 }
 
+// The library allocates through the device's default stream-ordered pool.  By default that
+// pool returns freed memory to the system at every synchronisation, so an index built after
+// another was destroyed would map its memory again; keep freed memory cached in the pool
+// instead (once per device), as a caching allocator does.
+static void keep_pool_memory()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st)
 {
     *p = nullptr;
+    keep_pool_memory();
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
@@ -131,7 +150,9 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
         SFC_TRY(reserve_sort(idx->sort_ws, std::max<uint64_t>(m, 1), st));
     }
     const uint64_t budget = (uint64_t)idx->opt.mask_budget_mb << 20;
-    uint64_t want = m * 4096ull + (1ull << 20);
+    // one bit per scanned point: 1 KB per query covers batches whose mean scan is up to 8,192
+    // points; chunks past the buffer are re-filtered by the write pass
+    uint64_t want = m * 1024ull + (1ull << 20);
     if (want > budget) want = budget;
     if (w.masks.bytes < want) SFC_TRY(w.masks.ensure(want, st));
     return SFC_OK;

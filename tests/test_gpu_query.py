@@ -146,6 +146,20 @@ def test_host_buffer_api(cuda, curve):
     assert e.value.status == sfc.SFC_ERR_CAPACITY
 
 
+def test_host_buffer_api_pinned_output(cuda):
+    """Pinned and pageable host output buffers both receive the oracle's answer."""
+    wl = W.mixed_1e7(scale=0.003)
+    idx = sfc.sfc_build_host(wl.points, "z")
+    roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta)
+    total = int(roff[-1])
+    pinned = torch.full((total,), -1, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    off, ids = sfc.sfc_query_batch_host(idx, wl.queries, wl.delta, total, out_ids=pinned)
+    assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+    pageable = np.full(total, 7, np.uint32)
+    off, ids = sfc.sfc_query_batch_host(idx, wl.queries, wl.delta, total, out_ids=pageable)
+    assert np.array_equal(ids, rids)
+
+
 def test_roads_scaled(cuda):
     wl = W.roads_3e7(scale=0.005)
     assert_same(wl.points, wl.queries, wl.delta, "h", cuda)
