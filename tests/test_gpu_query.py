@@ -193,3 +193,21 @@ def test_autotune(cuda):
     off, ids = sfc.query(idx2, q, d)
     roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta)
     assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+def test_extreme_radii(cuda, curve):
+    """Queries whose disc covers the whole domain (every point reported, the scan is the whole
+    array and spans hundreds of chunks), radius 0 on stacked duplicates, and tiny queries in the
+    same batch."""
+    rng = np.random.default_rng(12)
+    pts = rng.integers(0, 1 << 30, size=(200_000, 2)).astype(np.int32)
+    pts[:500] = [777, 999]                         # 500 duplicates of one point
+    qs = np.concatenate([np.array([[0, 0], [(1 << 30) - 1, 5], [777, 999], [777, 999]], np.int32),
+                         pts[rng.integers(0, 200_000, 300)]])
+    d = np.concatenate([np.array([2 ** 31 - 1, 1 << 30, 0, 3], np.int32),
+                        rng.integers(0, 1 << 16, 300).astype(np.int32)])
+    idx, st = assert_same(pts, qs, d, curve, cuda)
+    off = oracle.query(oracle.build(pts, 30, curve), qs[:3], d[:3])[0]
+    assert off[1] - off[0] == 200_000 and off[3] - off[2] == 500
+    assert st == (0, 0)
