@@ -49,6 +49,9 @@ def parse():
                     help="the headline is mixed-1e7; the others are supplementary measurements")
     ap.add_argument("--reorder", type=int, choices=[0, 1, 2], default=None,
                     help="query processing order (0 input, 1 curve, 2 automatic)")
+    ap.add_argument("--leaves", type=int, default=None, help="leaf segments of the learned model")
+    ap.add_argument("--cover", type=int, choices=[-1, 0, 1, 2], default=-1,
+                    help="cover of each query's ball: 0 cells(Q), 1/2 levels finer, -1 autotuned")
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -151,6 +154,10 @@ def run_ours(args, rank, world, local):
     opts = dict(bounds=bounds, profile=1)
     if args.reorder is not None:
         opts["reorder_queries"] = args.reorder
+    if args.cover is not None:
+        opts["cover_refine"] = args.cover
+    if args.leaves is not None:
+        opts["leaves"] = args.leaves
 
     # size the output once (the total is the same for every step) and let the autotuner pick
     # the scan's chunk size and work-queue batches for this shape (cached for later builds)
@@ -243,10 +250,13 @@ def run_ours(args, rank, world, local):
         },
     }
     if rank == 0 and not args.no_extras:
-        out["breakdown"].update(extras(sfc, torch, pts, q, d, total, n, m, flush))
-        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args)
+        bopts = {"cover_refine": tuned["cover"]}
+        if args.leaves is not None:
+            bopts["leaves"] = args.leaves
+        out["breakdown"].update(extras(sfc, torch, pts, q, d, total, n, m, flush, bopts))
+        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args, tuned["cover"])
     elif rank == 0:
-        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args)
+        out["e2e"] = e2e(sfc, torch, wl, total, bounds, args, tuned["cover"])
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, budget_s=20.0)
     if rank == 0:
@@ -325,16 +335,19 @@ def timed(fn, torch, flush, reps=3):
     return best
 
 
-def extras(sfc, torch, pts, q, d, total, n, m, flush):
+def extras(sfc, torch, pts, q, d, total, n, m, flush, bopts):
     """Untimed-for-the-headline measurements: query phase with binary vs learned bounds,
-    Hilbert build and query, and the learned model's window statistics."""
+    Hilbert build and query, and the learned model's window statistics (indexes built with
+    the step's cover and model options, tuned settings applied)."""
     out = {}
     off = torch.empty(m + 1, dtype=torch.int64, device=pts.device)
     ids = torch.empty(max(total, 1), dtype=torch.int32, device=pts.device)
     for curve in ("z", "h"):
-        build_ms = timed(lambda: sfc.sfc_build(pts, curve).close(), torch, flush)
-        ix = sfc.sfc_build(pts, curve)
-        res = {"build_ms": build_ms, "build_pts_per_s": n / (build_ms / 1e3)}
+        build_ms = timed(lambda: sfc.sfc_build(pts, curve, **bopts).close(), torch, flush)
+        ix = sfc.sfc_build(pts, curve, **bopts)
+        sfc.sfc_autotune(ix, q, d)
+        res = {"build_ms": build_ms, "build_pts_per_s": n / (build_ms / 1e3),
+               "cover": sfc.sfc_cover_refine(ix)}
         modes = ["binary"]
         try:
             sfc.sfc_train_model(ix)
@@ -392,7 +405,7 @@ def update_round(sfc, torch, pts, flush):
             "note": "includes the host validation sync and the learned-model refit"}
 
 
-def e2e(sfc, torch, wl, total, bounds, args):
+def e2e(sfc, torch, wl, total, bounds, args, cover):
     """The same step through the C ABI with host buffers: sfc_build_host + (model fit) +
     sfc_query_batch_host, host->device and device->host copies inside the timed region,
     inputs in pinned host memory."""
@@ -409,7 +422,7 @@ def e2e(sfc, torch, wl, total, bounds, args):
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = sfc.sfc_build_host(hp, "z", bounds=bounds)
+        ix = sfc.sfc_build_host(hp, "z", bounds=bounds, cover_refine=cover)
         sfc.sfc_query_batch_host(ix, hq, hd, total, out_offsets=hoff, out_ids=hids)
         ix.close()
         torch.cuda.synchronize()

@@ -79,6 +79,12 @@ typedef struct {
                                the coordinates outgrow L2, n >= 2^24 (default 2) */
     int profile;            /* 1 = record per-step CUDA events from the start (sfc_profile_read) */
     sfc_root root;          /* learned model: root kind (default SFC_ROOT_PWL) */
+    int cover_refine;       /* cover of each query's ball (outputs are unaffected): 0 the cells
+                               of cells(Q) (Alg. 1, at most 4 cells of level l with
+                               2 delta <= 2^l < 4 delta); 1 or 2 the cells of level l - 1 or
+                               l - 2 (at most 9 or 25) that hold an integer point of the closed
+                               ball, so fewer points are scanned for more key intervals; -1 the
+                               choice of sfc_autotune (1 until it runs) (default 0) */
 } sfc_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -180,19 +186,35 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
  * allocate nothing (needed before capturing them in a CUDA graph). */
 sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream);
 
-/* Autotuner: times the count pass (plan + scan + count) of this query batch for chunk sizes
- * {256, 512, 1024, 2048, 4096} points (threads-per-query granularity of the scan), then the
- * number of chunks taken per work-queue grab {1, 2, 4, 8, 16}, then the queries per write-pass
- * grab {1, 2, 4, 8, 16}, and keeps the fastest in the index (results do not depend on them).
- * The choice is cached per (device, curve, log2 n, log2 m) for later indexes; force != 0
- * re-measures.  Writes the choice to *h_chunk, *h_batch, *h_qbatch (any may be NULL).
- * Synchronises `stream`; allocates a temporary output buffer. */
+/* Autotuner: when the index was built with cover_refine = -1, first times whole batches
+ * (count + write) under the covers 0, 1 and 2; then times the count pass (plan + scan + count)
+ * of this query batch for chunk sizes {256, 512, 1024, 2048, 4096} points (threads-per-query
+ * granularity of the scan), then the number of chunks taken per work-queue grab
+ * {1, 2, 4, 8, 16}, then the queries per write-pass grab {1, 2, 4, 8, 16}, and keeps the
+ * fastest in the index (results do not depend on them).  The choice is cached per (device,
+ * curve, log2 n, log2 m, bound search, cover option) for later indexes; force != 0
+ * re-measures.  Writes the choice to *h_chunk, *h_batch, *h_qbatch (any may be NULL); the
+ * cover is read back with sfc_cover_refine.  Synchronises `stream`; allocates temporary
+ * output buffers. */
 sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m, int force,
                         int* h_chunk, int* h_batch, int* h_qbatch, void* stream);
 
 /* Chooses the bound search of later queries.  SFC_BOUNDS_LEARNED requires a trained model
  * (sfc_train_model or opt->bounds at build), else SFC_ERR_STATE. */
 sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);
+
+/* Sets the cover of later queries (0, 1 or 2 as opt->cover_refine; else SFC_ERR_INVALID).
+ * A count already made keeps its own cover for its write.  A captured query graph keeps the
+ * cover it was captured with; reserve (sfc_reserve_queries) after a change to a finer cover,
+ * since the per-query interval table grows with it. */
+sfc_status sfc_set_cover(sfc_index* idx, int refine);
+
+/* The cover currently used by queries (0, 1 or 2), or -1 for idx == NULL. */
+int sfc_cover_refine(const sfc_index* idx);
+
+/* Interval slots per query of the current cover: 4, 9 or 25 (0 for idx == NULL); the stride
+ * of sfc_query_ranges' outputs. */
+int sfc_query_max_intervals(const sfc_index* idx);
 
 /* ---------------------------------------------------------------------------------- */
 /* Learned bounds: two-stage CDF model replacing the search tree over the keys          */
@@ -305,10 +327,12 @@ sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out,
  * be serialised by the caller.  Output: d_out uint64[n+1] as sfc_exclusive_scan. */
 sfc_status sfc_exclusive_scan_noalloc(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
 
-/* Ranges and bounds of a query batch (Alg. 1 lines 1-4): for each query i, up to four
- * merged key intervals of cells(Q) (d_lo/d_hi uint64[4m], unused slots lo = 1, hi = 0) and
- * their array bounds by the index's current bound search (d_begin/d_end uint32[4m]);
- * d_count uint32[m] receives the number of intervals. Any output may be NULL. */
+/* Ranges and bounds of a query batch (Alg. 1, range derivation and bound search): for each
+ * query i, the merged key intervals of its cover -- cells(Q), or the finer cover set by
+ * cover_refine -- in K = sfc_query_max_intervals(idx) slots (d_lo/d_hi uint64[K m], slot
+ * K i + r, unused slots lo = 1, hi = 0) and their array bounds by the index's current bound
+ * search (d_begin/d_end uint32[K m]); d_count uint32[m] receives the number of intervals.
+ * Any output may be NULL. */
 sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta,
                             uint64_t m, uint64_t* d_lo, uint64_t* d_hi, uint32_t* d_begin,
                             uint32_t* d_end, uint32_t* d_count, void* stream);

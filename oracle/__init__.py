@@ -74,6 +74,8 @@ def _L():
         lib.oracle_level.argtypes = [ctypes.c_int64, c_int]
         lib.oracle_cells.restype = c_int
         lib.oracle_cells.argtypes = [i32, i32, i32, c_int, c_int, P, P, P]
+        lib.oracle_cells_refined.restype = c_int
+        lib.oracle_cells_refined.argtypes = [i32, i32, i32, c_int, c_int, c_int, P, P, c_int]
         lib.oracle_query.restype = c_int
         lib.oracle_query.argtypes = [P, P, P, u64, P, P, u64, c_int, c_int, P, P, P, P, c_int]
         lib.oracle_brute.restype = c_int
@@ -155,6 +157,29 @@ def cells(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z"):
     if cnt < 0:
         raise AssertionError("more than four cells")
     return [(int(lo[i]), int(hi[i])) for i in range(cnt)], int(lv.value)
+
+
+def cells_refined(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z", drop: int = 1):
+    """Key intervals of the cells one (or `drop`) quadtree levels below cells(Q) that contain
+    an integer point of the closed ball, sorted by lo (not merged)."""
+    maxc = (2 ** drop + 1) ** 2
+    lo = np.zeros(maxc, np.uint64)
+    hi = np.zeros(maxc, np.uint64)
+    cnt = _L().oracle_cells_refined(int(qx), int(qy), int(delta), int(w), curve_id(curve), int(drop),
+                                    _ptr(lo), _ptr(hi), maxc)
+    if cnt < 0:
+        raise AssertionError("more cells than (2^drop + 1)^2")
+    return [(int(lo[i]), int(hi[i])) for i in range(cnt)]
+
+
+def merge_abutting(intervals):
+    out = []
+    for a, z in intervals:
+        if out and out[-1][1] + 1 == a:
+            out[-1] = (out[-1][0], z)
+        else:
+            out.append((a, z))
+    return out
 
 
 def query(index: Index, q: np.ndarray, delta: np.ndarray, threads: int = 1, want_scanned=False):

@@ -199,6 +199,51 @@ int oracle_cells(int32_t qx, int32_t qy, int32_t delta, int w, int curve,
     return cnt;
 }
 
+/* Refined cover (a finer quadtree level than cells(Q), Sec. 2 "Efficiency" notes the cover's
+ * volume can be 2 * 2^d times that of Q): the cells at level l' = max(0, l - drop), where l is
+ * the level of cells(Q), that contain at least one integer point of the closed ball
+ * B_delta(q) within the domain; returns how many (at most (2^drop + 1)^2), key intervals
+ * sorted by lo, not merged.  drop = 0 keeps only cells(Q)'s cells that meet the ball. */
+int oracle_cells_refined(int32_t qx, int32_t qy, int32_t delta, int w, int curve, int drop,
+                         uint64_t* lo, uint64_t* hi, int maxc)
+{
+    int64_t side = (int64_t)1 << w;
+    int64_t d = delta;
+    int64_t x0 = (int64_t)qx - d, x1 = (int64_t)qx + d;
+    int64_t y0 = (int64_t)qy - d, y1 = (int64_t)qy + d;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > side - 1) x1 = side - 1;
+    if (y1 > side - 1) y1 = side - 1;
+    int l = oracle_level(d, w) - drop;
+    if (l < 0) l = 0;
+    int cnt = 0;
+    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
+        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
+            /* nearest integer point of the cell to q */
+            int64_t ax0 = cx << l, ax1 = ((cx + 1) << l) - 1;
+            int64_t ay0 = cy << l, ay1 = ((cy + 1) << l) - 1;
+            int64_t dx = 0, dy = 0;
+            if (qx < ax0) dx = ax0 - qx; else if (qx > ax1) dx = qx - ax1;
+            if (qy < ay0) dy = ay0 - qy; else if (qy > ay1) dy = qy - ay1;
+            if (dx * dx + dy * dy > d * d) continue;
+            if (cnt == maxc) return -1;
+            uint64_t corner = oracle_key((uint32_t)(cx << l), (uint32_t)(cy << l), w, curve);
+            uint64_t span = ((uint64_t)1 << (2 * l)) - 1;
+            lo[cnt] = (corner >> (2 * l)) << (2 * l);
+            hi[cnt] = lo[cnt] + span;
+            ++cnt;
+        }
+    }
+    for (int i = 1; i < cnt; ++i) {
+        uint64_t a = lo[i], b = hi[i];
+        int j = i - 1;
+        while (j >= 0 && lo[j] > a) { lo[j + 1] = lo[j]; hi[j + 1] = hi[j]; --j; }
+        lo[j + 1] = a; hi[j + 1] = b;
+    }
+    return cnt;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Query, Alg. 1: for each cell (in key order) lower_bound the start of its interval, scan */
 /* while the key is <= pi(C)o1 (inclusive end, Observation), and report every point with  */

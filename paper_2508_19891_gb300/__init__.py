@@ -48,7 +48,8 @@ class sfc_options(ctypes.Structure):
     _fields_ = [("bounds", ctypes.c_int), ("leaves", ctypes.c_int), ("train_steps", ctypes.c_int),
                 ("train_samples", ctypes.c_int), ("learning_rate", ctypes.c_float),
                 ("chunk", ctypes.c_int), ("mask_budget_mb", ctypes.c_int),
-                ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int), ("root", ctypes.c_int)]
+                ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int), ("root", ctypes.c_int),
+                ("cover_refine", ctypes.c_int)]
 
 
 class sfc_profile_entry(ctypes.Structure):
@@ -85,6 +86,9 @@ def lib():
             "sfc_query_batch_host": (ci, [P, P, P, u64, P, P, u64, P]),
             "sfc_reserve_queries": (ci, [P, u64, P]),
             "sfc_set_bounds_mode": (ci, [P, ci]),
+            "sfc_set_cover": (ci, [P, ci]),
+            "sfc_cover_refine": (ci, [P]),
+            "sfc_query_max_intervals": (ci, [P]),
             "sfc_train_model": (ci, [P, P]),
             "sfc_model_hidden": (ci, []),
             "sfc_model_params": (ci, [ci]),
@@ -373,7 +377,8 @@ def sfc_autotune(index: Index, q: torch.Tensor, delta: torch.Tensor, force: bool
     c, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().sfc_autotune(index.handle, _dptr(q), _dptr(delta), q.shape[0], int(bool(force)), ctypes.byref(c),
                               ctypes.byref(b), ctypes.byref(w), _stream(stream)), "sfc_autotune")
-    return {"chunk": c.value, "batch": b.value, "qbatch": w.value}
+    return {"chunk": c.value, "batch": b.value, "qbatch": w.value,
+            "cover": int(lib().sfc_cover_refine(index.handle))}
 
 
 def sfc_reserve_queries(index: Index, m: int, stream=None):
@@ -382,6 +387,18 @@ def sfc_reserve_queries(index: Index, m: int, stream=None):
 
 def sfc_set_bounds_mode(index: Index, mode):
     _check(lib().sfc_set_bounds_mode(index.handle, _bounds(mode)), "sfc_set_bounds_mode")
+
+
+def sfc_set_cover(index: Index, refine: int):
+    _check(lib().sfc_set_cover(index.handle, int(refine)), "sfc_set_cover")
+
+
+def sfc_cover_refine(index: Index) -> int:
+    return int(lib().sfc_cover_refine(index.handle))
+
+
+def sfc_query_max_intervals(index: Index) -> int:
+    return int(lib().sfc_query_max_intervals(index.handle))
 
 
 def sfc_train_model(index: Index, stream=None):
@@ -550,10 +567,11 @@ def sfc_query_ranges(index: Index, q: torch.Tensor, delta: torch.Tensor, stream=
     delta = delta.contiguous()
     m = q.shape[0]
     dev = q.device
-    lo = torch.empty(4 * m, dtype=torch.int64, device=dev)
-    hi = torch.empty(4 * m, dtype=torch.int64, device=dev)
-    b = torch.empty(4 * m, dtype=torch.int32, device=dev)
-    e = torch.empty(4 * m, dtype=torch.int32, device=dev)
+    k = sfc_query_max_intervals(index)
+    lo = torch.empty(k * m, dtype=torch.int64, device=dev)
+    hi = torch.empty(k * m, dtype=torch.int64, device=dev)
+    b = torch.empty(k * m, dtype=torch.int32, device=dev)
+    e = torch.empty(k * m, dtype=torch.int32, device=dev)
     c = torch.empty(m, dtype=torch.int32, device=dev)
     _check(lib().sfc_query_ranges(index.handle, _dptr(q), _dptr(delta), m, _dptr(lo), _dptr(hi), _dptr(b),
                                   _dptr(e), _dptr(c), _stream(stream)), "sfc_query_ranges")

@@ -130,13 +130,15 @@ QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint
     a.delta = delta;
     a.m = m;
     a.status = status_word(idx);
+    a.drop = idx->drop;
+    a.kint = (uint32_t)cover_intervals(idx->drop);
     return a;
 }
 
 sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
 {
     QueryWs& w = idx->qws;
-    SFC_TRY(w.ranges.ensure(m * 8 * sizeof(uint32_t), st));
+    SFC_TRY(w.ranges.ensure(m * 2 * cover_intervals(idx->drop) * sizeof(uint32_t), st));
     SFC_TRY(w.nchunks.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
@@ -182,7 +184,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     SFC_TRY(ensure_status_buf(idx, st));
     if (m == 0) {
         SFC_CUDA_TRY(cudaMemsetAsync(d_out_offsets, 0, sizeof(uint64_t), st));
-        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0, false};
+        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0, false, idx->drop};
         return SFC_OK;
     }
     SFC_TRY(ensure_query_ws(idx, m, st));
@@ -242,7 +244,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         ProfScope ps(idx, "scan", st);
         SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
     }
-    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered};
+    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered, a.drop};
     return SFC_OK;
 }
 
@@ -256,6 +258,8 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     w.pending.valid = false;
     if (m == 0) return SFC_OK;
     QueryArgs a = base_args(idx, d_q, d_delta, m);
+    a.drop = w.pending.drop;
+    a.kint = (uint32_t)cover_intervals(a.drop);
     a.ranges = w.ranges.as<uint32_t>();
     a.nchunks = w.nchunks.as<uint32_t>();
     a.chunk_base = w.chunk_base.as<uint64_t>();
@@ -296,6 +300,7 @@ void sfc_default_options(sfc_options* opt)
     opt->reorder_queries = 2;
     opt->profile = 0;
     opt->root = SFC_ROOT_PWL;
+    opt->cover_refine = 0;
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
@@ -311,7 +316,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     if (o.leaves < 1 || o.leaves > (1 << 20) || o.mask_budget_mb < 1 || o.train_samples < 2 ||
         o.train_steps < 0 || o.reorder_queries < 0 || o.reorder_queries > 2 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
         (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED) ||
-        (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP))
+        (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP) || o.cover_refine < -1 || o.cover_refine > 2)
         return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     sfc_index* idx = new (std::nothrow) sfc_index();
@@ -322,6 +327,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     idx->opt = o;
     idx->bounds = SFC_BOUNDS_BINARY;
     idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;
+    idx->drop = o.cover_refine < 0 ? 1 : o.cover_refine;
     idx->last_stream = st;
     idx->prof.on = o.profile != 0;
     sfc_status s = ensure_status_buf(idx, st);
@@ -494,15 +500,17 @@ sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_
 namespace {
 
 struct TuneKey {
-    int device, curve, lgn, lgm, bounds;
+    int device, curve, lgn, lgm, bounds, cover;   // cover: the option (-1 = tuned)
     bool operator==(const TuneKey& o) const
     {
-        return device == o.device && curve == o.curve && lgn == o.lgn && lgm == o.lgm && bounds == o.bounds;
+        return device == o.device && curve == o.curve && lgn == o.lgn && lgm == o.lgm && bounds == o.bounds &&
+               cover == o.cover;
     }
 };
 
 struct TuneVal {
     uint32_t chunk, batch, qbatch;
+    int drop;
 };
 
 std::mutex g_tune_mu;
@@ -548,7 +556,8 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
 {
     if (!idx || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
-    const TuneKey key{idx->device, (int)idx->curve, lg2(idx->n + 1), lg2(m + 1), (int)idx->bounds};
+    const TuneKey key{idx->device, (int)idx->curve, lg2(idx->n + 1), lg2(m + 1), (int)idx->bounds,
+                      idx->opt.cover_refine};
     bool cached = false;
     if (!force) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -557,17 +566,42 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
                 idx->chunk = kv.second.chunk;
                 idx->batch = kv.second.batch;
                 idx->qbatch = kv.second.qbatch;
+                idx->drop = kv.second.drop;
                 cached = true;
             }
     }
     if (!cached && m > 0) {
         const bool prof = idx->prof.on;
         idx->prof.on = false;
-        DevBuf off;
+        DevBuf off, ids;
         sfc_status s = off.ensure((m + 1) * sizeof(uint64_t), st);
         auto count = [&]() { return do_count(idx, d_q, d_delta, m, off.as<uint64_t>(), st); };
+        auto write = [&](uint64_t total) {
+            return do_write(idx, d_q, d_delta, m, off.as<uint64_t>(), ids.as<uint32_t>(), total, st);
+        };
+        // the result (and so its size) is the same under every setting
+        uint64_t total = 0;
+        if (s == SFC_OK) s = count();
+        if (s == SFC_OK && cudaMemcpyAsync(&total, off.as<uint64_t>() + m, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess) s = SFC_ERR_CUDA;
+        if (s == SFC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SFC_ERR_CUDA;
+        if (s == SFC_OK) s = ids.ensure(std::max<uint64_t>(total, 1) * sizeof(uint32_t), st);
+        idx->qws.pending.valid = false;
         float best = 1e30f, t = 0.0f;
+        int bd = idx->drop;
+        if (idx->opt.cover_refine < 0) {   // the cover: whole batches (both passes) per candidate
+            for (int d : {0, 1, 2}) {
+                if (s != SFC_OK) break;
+                idx->drop = d;
+                s = time_on(st, 2, &t, [&]() {
+                    sfc_status c = count();
+                    return c == SFC_OK ? write(total) : c;
+                });
+                if (t < best) { best = t; bd = d; }
+            }
+            idx->drop = bd;
+        }
         uint32_t bc = idx->chunk, bb = idx->batch, bq = idx->qbatch;
+        best = 1e30f;
         for (uint32_t c : {256u, 512u, 1024u, 2048u, 4096u}) {
             if (s != SFC_OK) break;
             idx->chunk = c;
@@ -585,19 +619,14 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
         }
         idx->batch = bb;
         // write pass: one count with the chosen settings, then time the writes
-        uint64_t total = 0;
         if (s == SFC_OK) s = count();
-        if (s == SFC_OK && cudaMemcpyAsync(&total, off.as<uint64_t>() + m, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess) s = SFC_ERR_CUDA;
-        if (s == SFC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SFC_ERR_CUDA;
-        DevBuf ids;
-        if (s == SFC_OK) s = ids.ensure(std::max<uint64_t>(total, 1) * sizeof(uint32_t), st);
         best = 1e30f;
         for (uint32_t qb : {1u, 2u, 4u, 8u, 16u}) {
             if (s != SFC_OK) break;
             idx->qbatch = qb;
             s = time_on(st, 2, &t, [&]() {
                 idx->qws.pending.valid = true;   // the plan of the last count is still in place
-                return do_write(idx, d_q, d_delta, m, off.as<uint64_t>(), ids.as<uint32_t>(), total, st);
+                return write(total);
             });
             if (t < best) { best = t; bq = qb; }
         }
@@ -611,14 +640,25 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
         std::lock_guard<std::mutex> lock(g_tune_mu);
         bool found = false;
         for (auto& kv : g_tune_cache)
-            if (kv.first == key) { kv.second = TuneVal{bc, bb, bq}; found = true; }
-        if (!found) g_tune_cache.push_back({key, TuneVal{bc, bb, bq}});
+            if (kv.first == key) { kv.second = TuneVal{bc, bb, bq, bd}; found = true; }
+        if (!found) g_tune_cache.push_back({key, TuneVal{bc, bb, bq, bd}});
     }
     if (h_chunk) *h_chunk = (int)idx->chunk;
     if (h_batch) *h_batch = (int)idx->batch;
     if (h_qbatch) *h_qbatch = (int)idx->qbatch;
     return SFC_OK;
 }
+
+sfc_status sfc_set_cover(sfc_index* idx, int refine)
+{
+    if (!idx || refine < 0 || refine > 2) return SFC_ERR_INVALID;
+    idx->drop = refine;
+    return SFC_OK;
+}
+
+int sfc_query_max_intervals(const sfc_index* idx) { return idx ? cover_intervals(idx->drop) : 0; }
+
+int sfc_cover_refine(const sfc_index* idx) { return idx ? idx->drop : -1; }
 
 sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta, uint64_t m,
                                 uint64_t* h_out_offsets, uint32_t* h_out_ids, uint64_t ids_capacity,

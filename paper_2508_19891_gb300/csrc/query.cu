@@ -2,10 +2,12 @@
 //
 //   plan_kernel    one thread per query: bounding square Q of B_delta(q), the level l with
 //                  2 delta <= 2^l < 4 delta, the <= 4 cells of cells(Q) and their key
-//                  intervals [pi(C)o0, pi(C)o1] (Observation), sorted and with abutting
-//                  intervals merged, then lower_bound of both ends of every interval, by
-//                  binary search or by the learned model (verified, with fallback).  The
-//                  query's scan length S_q is cut into chunks of C points.
+//                  intervals [pi(C)o0, pi(C)o1] (Observation) -- or, with a refined cover,
+//                  the cells one or two levels finer (<= 9 / <= 25) that meet the ball --
+//                  sorted and with abutting intervals merged, then lower_bound of both ends
+//                  of every interval, by binary search or by the learned model (verified,
+//                  with fallback).  The query's scan length S_q is cut into chunks of C
+//                  points.
 //   scan           exclusive scan of the chunk counts -> chunk bases.
 //   count_kernel   persistent warps take batches of chunks from a counter (work stealing);
 //                  a warp streams the chunk's coordinates, applies the exact int64 filter
@@ -17,7 +19,10 @@
 //                  the filter) and writes the ids of the hits with ballot/popc compaction at
 //                  out_offsets[q] + rank, so each query's ids come out in array order.
 //
-// The bitmask makes the second pass read 1 bit instead of 8 bytes per scanned point.
+// The bitmask makes the second pass read 1 bit instead of 8 bytes per scanned point.  In the
+// two scan passes a warp keeps its query's intervals (array shift and end of each, in the
+// concatenated order of the scan) in shared memory; a lane moves to the next interval only
+// when its index crosses the current one's end.
 #include "sfc_internal.cuh"
 #include "query.cuh"
 
@@ -26,54 +31,6 @@ namespace sfc {
 namespace {
 
 constexpr int kThreads = 256;
-
-// ------------------------------------------------------------------------------------
-// Ranges (cells(Q) with merged abutting intervals)
-// ------------------------------------------------------------------------------------
-struct QueryRanges {
-    uint64_t lo[4], hi[4];
-    int cnt;
-};
-
-__device__ __forceinline__ void derive_ranges(int curve, const HilbertTables* tb, int32_t qx,
-                                              int32_t qy, int32_t delta, QueryRanges& R)
-{
-    const int64_t d = delta;
-    const int64_t x0 = max((int64_t)0, (int64_t)qx - d), x1 = min((int64_t)kSide - 1, (int64_t)qx + d);
-    const int64_t y0 = max((int64_t)0, (int64_t)qy - d), y1 = min((int64_t)kSide - 1, (int64_t)qy + d);
-    int l = 0;
-    if (d > 0) {
-        l = 64 - __clzll((unsigned long long)(2 * d - 1));   // bit length of 2 delta - 1
-        if (l > kOmega) l = kOmega;
-    }
-    const uint64_t span = (l >= kOmega) ? kKeyMax : ((1ull << (2 * l)) - 1);
-    int cnt = 0;
-    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
-        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
-            if (cnt == 4) break;   // unreachable: x1 - x0 <= 2 delta <= 2^l gives <= 2 per axis
-            uint64_t k = curve_key(curve, tb, (uint32_t)(cx << l), (uint32_t)(cy << l));
-            uint64_t lo = k & ~span;
-            // insertion in lo order
-            int j = cnt;
-            while (j > 0 && R.lo[j - 1] > lo) { R.lo[j] = R.lo[j - 1]; R.hi[j] = R.hi[j - 1]; --j; }
-            R.lo[j] = lo;
-            R.hi[j] = lo | span;
-            ++cnt;
-        }
-    }
-    // merge intervals that abut in key order (the scan over them is identical)
-    int m = 0;
-    for (int i = 0; i < cnt; ++i) {
-        if (m > 0 && R.hi[m - 1] + 1 == R.lo[i]) {
-            R.hi[m - 1] = R.hi[i];
-        } else {
-            R.lo[m] = R.lo[i];
-            R.hi[m] = R.hi[i];
-            ++m;
-        }
-    }
-    R.cnt = m;
-}
 
 __device__ __forceinline__ bool query_valid(int32_t qx, int32_t qy, int32_t delta)
 {
@@ -107,21 +64,30 @@ __device__ __forceinline__ void lower_bounds_window(const uint64_t* __restrict__
     }
 }
 
+// Per-thread counters of the learned search, summed once per block at the end of the plan.
+struct BoundStats {
+    unsigned long long endpoints = 0, misses = 0, window = 0;
+};
+
+// Bound search functors: lower_bound of t[0..ne) (ne <= E) into r[].
 struct BinaryBounds {
+    static constexpr bool kStats = false;
     __device__ __forceinline__ void prepare(RootParams*) {}
-    __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
-                                               uint32_t* r, int ne) const
+    template <int E>
+    __device__ __forceinline__ void search(const uint64_t* keys, uint32_t n, const uint64_t* t, uint32_t* r,
+                                           int ne, BoundStats&) const
     {
-        uint32_t lo[8], len[8];
+        uint32_t lo[E], len[E];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) { lo[e] = 0; len[e] = e < ne ? n : 0; }
-        lower_bounds_window<8>(keys, t, lo, len);
+        for (int e = 0; e < E; ++e) { lo[e] = 0; len[e] = e < ne ? n : 0; }
+        lower_bounds_window<E>(keys, t, lo, len);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = lo[e];
+        for (int e = 0; e < E; ++e) r[e] = lo[e];
     }
 };
 
 struct LearnedBounds {
+    static constexpr bool kStats = true;
     const RootParams* root;      // device; after prepare() the block's shared-memory copy
     const LeafParams* leaf;
     unsigned long long* stats;   // [0] endpoints, [1] misses, [2] window sum
@@ -133,13 +99,14 @@ struct LearnedBounds {
         for (unsigned i = threadIdx.x; i < sizeof(RootParams) / 4; i += blockDim.x) dst[i] = src[i];
         root = s;
     }
-    __device__ __forceinline__ void operator()(const uint64_t* keys, uint32_t n, const uint64_t* t,
-                                               uint32_t* r, int ne) const
+    template <int E>
+    __device__ __forceinline__ void search(const uint64_t* keys, uint32_t n, const uint64_t* t, uint32_t* r,
+                                           int ne, BoundStats& bs) const
     {
-        uint32_t lo[8], len[8];
+        uint32_t lo[E], len[E];
         unsigned long long wsum = 0;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < E; ++e) {
             lo[e] = 0;
             len[e] = 0;
             if (e < ne) {
@@ -156,144 +123,276 @@ struct LearnedBounds {
                 wsum += len[e];
             }
         }
-        lower_bounds_window<8>(keys, t, lo, len);
-        // verify: lower_bound is the unique r with keys[r-1] < t <= keys[r]
+        // window search, verify (lower_bound is the unique r with keys[r-1] < t <= keys[r]), and
+        // for the endpoints that fail, a second pass over the whole array (full binary search)
         uint32_t miss = 0;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            lower_bounds_window<E>(keys, t, lo, len);
+            if (pass == 1) break;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            if (e < ne) {
-                const uint32_t x = lo[e];
-                const bool ok = (x == 0 || __ldg(keys + x - 1) < t[e]) && (x == n || __ldg(keys + x) >= t[e]);
-                if (!ok) { miss |= 1u << e; lo[e] = 0; len[e] = n; }
+            for (int e = 0; e < E; ++e) {
+                if (e < ne) {
+                    const uint32_t x = lo[e];
+                    const bool ok = (x == 0 || __ldg(keys + x - 1) < t[e]) && (x == n || __ldg(keys + x) >= t[e]);
+                    if (!ok) { miss |= 1u << e; lo[e] = 0; len[e] = n; }
+                }
             }
+            if (!miss) break;
         }
-        if (miss) lower_bounds_window<8>(keys, t, lo, len);   // full binary search fallback
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = lo[e];
-        if (stats) {
-            unsigned long long c = ne, mc = __popc(miss);
-            // one atomic per warp
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                c += __shfl_xor_sync(0xffffffffu, c, o);
-                mc += __shfl_xor_sync(0xffffffffu, mc, o);
-                wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-            }
-            if (lane_id() == 0) {
-                atomicAdd(stats + 0, c);
-                atomicAdd(stats + 1, mc);
-                atomicAdd(stats + 2, wsum);
-            }
-        }
+        for (int e = 0; e < E; ++e) r[e] = lo[e];
+        bs.endpoints += ne;
+        bs.misses += __popc(miss);
+        bs.window += wsum;
     }
 };
 
-// Range derivation + bound search for one query; returns the merged intervals' bounds.
-template <class Bounds>
-__device__ __forceinline__ int query_bounds(const Bounds& bounds, int curve, const HilbertTables* tb,
-                                            const uint64_t* keys, uint32_t n, bool ok, int32_t qx,
-                                            int32_t qy, int32_t delta, QueryRanges& R, uint32_t* b,
-                                            uint32_t* e)
+// Sum of v over the warp (every lane calls), returned to every lane.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
-    R.cnt = 0;
-    if (ok) derive_ranges(curve, tb, qx, qy, delta, R);
-    uint64_t t[8];
-    const int ne = 2 * R.cnt;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        t[2 * i] = i < R.cnt ? R.lo[i] : 0;
-        t[2 * i + 1] = i < R.cnt ? R.hi[i] + 1 : 0;
-    }
-    uint32_t r[8];
-    bounds(keys, n, t, r, ne);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        b[i] = i < R.cnt ? r[2 * i] : 0;
-        e[i] = i < R.cnt ? r[2 * i + 1] : 0;
-    }
-    return R.cnt;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // ------------------------------------------------------------------------------------
-// plan_kernel
+// plan_kernel: range derivation and bound search, one thread per query
 // ------------------------------------------------------------------------------------
-template <class Bounds>
-__global__ void __launch_bounds__(kThreads) plan_kernel(QueryArgs a, Bounds bounds_in)
+template <int DROP>
+struct Cover {
+    // cells per axis at most: 2 for cells(Q) (2 delta <= 2^l), 2^DROP + 1 one or two levels finer
+    static constexpr int NX = DROP == 0 ? 2 : (1 << DROP) + 1;
+    static constexpr int K = NX * NX;   // 4, 9, 25 interval slots per query
+};
+
+// Writes the cover's key intervals to lo/hi (sorted, abutting ones merged); returns how many.
+// DROP 0: cells(Q), the cells of level l (2 delta <= 2^l < 4 delta, capped at omega) that meet
+// the clipped square Q.  DROP > 0: the cells of level max(0, l - DROP) that hold an integer
+// point of the closed ball (the distance from q to the cell's nearest integer point is at most
+// delta).  Each cell gives the key interval [pi(C)o0, pi(C)o1] (Observation).
+template <int DROP>
+__device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb, int32_t qx, int32_t qy,
+                                             int32_t delta, uint64_t* lo, uint64_t* hi)
 {
+    constexpr int K = Cover<DROP>::K;
+    const int64_t d = delta;
+    const int64_t x0 = max((int64_t)0, (int64_t)qx - d), x1 = min((int64_t)kSide - 1, (int64_t)qx + d);
+    const int64_t y0 = max((int64_t)0, (int64_t)qy - d), y1 = min((int64_t)kSide - 1, (int64_t)qy + d);
+    int l = 0;
+    if (d > 0) {
+        l = 64 - __clzll((unsigned long long)(2 * d - 1));   // bit length of 2 delta - 1
+        if (l > kOmega) l = kOmega;
+    }
+    l = max(0, l - DROP);
+    const uint64_t span = (l >= kOmega) ? kKeyMax : ((1ull << (2 * l)) - 1);
+    int cnt = 0;
+    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
+        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
+            if (DROP > 0) {
+                const int64_t ax0 = cx << l, ax1 = ((cx + 1) << l) - 1;
+                const int64_t ay0 = cy << l, ay1 = ((cy + 1) << l) - 1;
+                const int64_t dx = qx < ax0 ? ax0 - qx : (qx > ax1 ? qx - ax1 : 0);
+                const int64_t dy = qy < ay0 ? ay0 - qy : (qy > ay1 ? qy - ay1 : 0);
+                if (dx * dx + dy * dy > d * d) continue;
+            }
+            if (cnt == K) break;   // unreachable: at most Cover<DROP>::NX cells per axis
+            const uint64_t c = curve_key(curve, tb, (uint32_t)(cx << l), (uint32_t)(cy << l)) & ~span;
+            int j = cnt;
+            while (j > 0 && lo[j - 1] > c) { lo[j] = lo[j - 1]; hi[j] = hi[j - 1]; --j; }
+            lo[j] = c;
+            hi[j] = c | span;
+            ++cnt;
+        }
+    }
+    // merge intervals that abut in key order (the scan over them is identical)
+    int m = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (m > 0 && hi[m - 1] + 1 == lo[i]) {
+            hi[m - 1] = hi[i];
+        } else {
+            lo[m] = lo[i];
+            hi[m] = hi[i];
+            ++m;
+        }
+    }
+    return m;
+}
+
+// Range derivation + bound search for one query: the intervals' key ranges lo/hi and array
+// bounds b[r], e[r]; returns their number.  Endpoints go through the bound search in lock-step
+// batches of 8 (eight independent searches in flight per thread).
+template <class Bounds, int DROP>
+__device__ __forceinline__ int query_bounds(const Bounds& bounds, int curve, const HilbertTables* tb,
+                                            const uint64_t* keys, uint32_t n, bool ok, int32_t qx,
+                                            int32_t qy, int32_t delta, uint64_t* lo, uint64_t* hi,
+                                            uint32_t* b, uint32_t* e, BoundStats& bs)
+{
+    constexpr int K = Cover<DROP>::K;
+    constexpr int NB = (2 * K + 7) / 8;
+    const int cnt = ok ? derive_ranges<DROP>(curve, tb, qx, qy, delta, lo, hi) : 0;
+    const int ne = 2 * cnt;
+#pragma unroll 1
+    for (int bi = 0; bi < NB && 8 * bi < ne; ++bi) {
+        uint64_t t[8];
+        uint32_t r[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int ep = 8 * bi + x;
+            t[x] = ep < ne ? ((ep & 1) ? hi[ep >> 1] + 1 : lo[ep >> 1]) : 0;
+        }
+        bounds.template search<8>(keys, n, t, r, min(max(ne - 8 * bi, 0), 8), bs);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int ep = 8 * bi + x;
+            if (ep < ne) {
+                if (ep & 1) e[ep >> 1] = r[x];
+                else b[ep >> 1] = r[x];
+            }
+        }
+    }
+    return cnt;
+}
+
+// Optional outputs of the plan (the ranges export); null in the query path.
+struct PlanExport {
+    uint64_t* lo;
+    uint64_t* hi;
+    uint32_t* b;
+    uint32_t* e;
+    uint32_t* cnt;
+};
+
+// One thread per query: its intervals' (begin, end) in slots 0.. of the query's K slots (unused
+// slots (0, 0)), the number of chunks of its scan, and the scanned total.
+template <class Bounds, int DROP, bool EXPORT>
+__global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds bounds_in, PlanExport ex)
+{
+    constexpr int K = Cover<DROP>::K;
     __shared__ HilbertTables tb;
     __shared__ RootParams s_root;
     Bounds bounds = bounds_in;
     bounds.prepare(&s_root);
     __syncthreads();
-    if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
+    if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);   // ends with a block barrier
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = i < a.m;
     int2 q = make_int2(0, 0);
     int32_t delta = -1;
     if (active) {
-        q = reinterpret_cast<const int2*>(a.q)[i];
-        delta = a.delta[i];
+        q = __ldg(reinterpret_cast<const int2*>(a.q) + i);
+        delta = __ldg(a.delta + i);
     }
     const bool ok = active && query_valid(q.x, q.y, delta);
     if (active && !ok) set_status(a.status, SFC_DEV_BAD_QUERY);
-    uint32_t b[4], e[4];
-    QueryRanges R;
-    // every lane calls the bound search (with no endpoints when inactive or invalid), so
-    // warp-collective statistics inside it see a converged warp
-    query_bounds(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, R, b, e);
+    uint64_t lo[K], hi[K];
+    uint32_t b[K], e[K];
+    BoundStats bs;
+    const int cnt = ok ? query_bounds<Bounds, DROP>(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, lo,
+                                                    hi, b, e, bs)
+                       : 0;
     uint64_t S = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) S += e[k] - b[k];
-    if (a.scanned) {   // one atomic per warp
-        unsigned long long ws = S;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
-        if (lane_id() == 0 && ws) atomicAdd(a.scanned, ws);
+    for (int k = 0; k < cnt; ++k) S += e[k] - b[k];
+    // warp totals of the statistics: one atomic per warp and counter, no block barrier (a warp
+    // that is done leaves without waiting for the rest of its block)
+    if (a.scanned) {
+        const unsigned long long t = warp_sum_u64(S);
+        if (lane_id() == 0 && t) atomicAdd(a.scanned, t);
+    }
+    if constexpr (Bounds::kStats) {
+        if (bounds.stats) {
+            const unsigned long long te = warp_sum_u64(bs.endpoints);
+            const unsigned long long tm = warp_sum_u64(bs.misses);
+            const unsigned long long tw = warp_sum_u64(bs.window);
+            if (lane_id() == 0 && te) {
+                atomicAdd(bounds.stats + 0, te);
+                if (tm) atomicAdd(bounds.stats + 1, tm);
+                atomicAdd(bounds.stats + 2, tw);
+            }
+        }
     }
     if (!active) return;
-    uint4* rp = reinterpret_cast<uint4*>(a.ranges + 8 * i);
-    rp[0] = make_uint4(b[0], e[0], b[1], e[1]);
-    rp[1] = make_uint4(b[2], e[2], b[3], e[3]);
-    a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+    if (!EXPORT) {
+        uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * K * i);
+#pragma unroll
+        for (int k = 0; k < K; ++k) rp[k] = k < cnt ? make_uint2(b[k], e[k]) : make_uint2(0u, 0u);
+        a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+    } else {
+        for (int k = 0; k < K; ++k) {
+            const bool u = k < cnt;
+            const uint64_t o = (uint64_t)K * i + k;
+            if (ex.lo) ex.lo[o] = u ? lo[k] : 1;
+            if (ex.hi) ex.hi[o] = u ? hi[k] : 0;
+            if (ex.b) ex.b[o] = u ? b[k] : 0;
+            if (ex.e) ex.e[o] = u ? e[k] : 0;
+        }
+        if (ex.cnt) ex.cnt[i] = (uint32_t)cnt;
+    }
 }
 
 // ------------------------------------------------------------------------------------
 // Shared helpers of the two scan passes
 // ------------------------------------------------------------------------------------
+constexpr int kMaxInt = 25;   // intervals per query at the finest cover
+
+// One query's intervals in the concatenated order of its scan (per-warp shared memory):
+// array position = concatenated index + shift[r] for indices below end[r].
+struct WarpTab {
+    uint32_t shift[kMaxInt];
+    uint32_t end[kMaxInt];
+};
+
 struct QView {
-    uint32_t b0, b1, b2, b3;
-    uint32_t c1, c2, c3, S;   // cumulative starts of intervals 1..3 and the total
+    uint32_t S;      // concatenated length (sum of the interval lengths)
+    uint32_t nint;   // intervals stored per query
     int2 q;
     int64_t d2;
 };
 
-__device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi)
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v += t;
+    }
+    return v;
+}
+
+// Loads query qi's intervals into the warp's table (lane r takes interval r); every lane calls.
+__device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi, WarpTab* tab)
 {
     QView v;
-    const uint4* rp = reinterpret_cast<const uint4*>(a.ranges + 8 * qi);
-    uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-    v.b0 = r0.x; v.b1 = r0.z; v.b2 = r1.x; v.b3 = r1.z;
-    v.c1 = r0.y - r0.x;
-    v.c2 = v.c1 + (r0.w - r0.z);
-    v.c3 = v.c2 + (r1.y - r1.x);
-    v.S = v.c3 + (r1.w - r1.z);
+    const unsigned lane = lane_id();
+    uint32_t b = 0, len = 0;
+    if (lane < a.kint) {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(a.ranges) + qi * a.kint + lane);
+        b = r.x;
+        len = r.y - r.x;
+    }
+    const uint32_t incl = warp_incl_scan_u32(len);
+    __syncwarp();   // the previous query's table is no longer read
+    if (lane < a.kint) {
+        tab->shift[lane] = b - (incl - len);
+        tab->end[lane] = incl;
+    }
+    __syncwarp();
+    v.S = __shfl_sync(0xffffffffu, incl, 31);
+    v.nint = a.kint;
     v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
     const int64_t d = __ldg(a.delta + qi);
     v.d2 = d * d;
     return v;
 }
 
-__device__ __forceinline__ uint32_t map_pos(const QView& v, uint32_t f)
+// Moves a lane's interval cursor r forward to the interval holding concatenated index f.
+__device__ __forceinline__ void seek(const WarpTab* tab, uint32_t nint, uint32_t f, uint32_t& r, uint32_t& shift,
+                                     uint32_t& end)
 {
-    return f < v.c1 ? v.b0 + f : f < v.c2 ? v.b1 + (f - v.c1) : f < v.c3 ? v.b2 + (f - v.c2) : v.b3 + (f - v.c3);
-}
-
-// Offset from concatenated index f to array position (mod 2^32) for the interval holding f,
-// and the first concatenated index of the next interval.
-__device__ __forceinline__ void interval_of(const QView& v, uint32_t f, uint32_t& shift, uint32_t& end)
-{
-    shift = f < v.c1 ? v.b0 : f < v.c2 ? v.b1 - v.c1 : f < v.c3 ? v.b2 - v.c2 : v.b3 - v.c3;
-    end = f < v.c1 ? v.c1 : f < v.c2 ? v.c2 : f < v.c3 ? v.c3 : 0xffffffffu;
+    while (r + 1 < nint && f >= tab->end[r]) ++r;
+    shift = tab->shift[r];
+    end = tab->end[r];
 }
 
 // Exact closed-ball test: |dx|, |dy| < 2^30, so each square is one signed 32x32 -> 64-bit
@@ -327,16 +426,16 @@ __device__ __forceinline__ void keep_words(uint32_t (&words)[WPL], uint32_t it, 
 // its interval (one vote), the group runs without per-point guards; otherwise each point is
 // checked and the lane looks its interval up again when it crosses into the next one.
 template <int WPL>
-__device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, uint32_t s0,
-                                                 uint32_t s1, uint32_t (&words)[WPL])
+__device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, const WarpTab* tab,
+                                                 uint32_t s0, uint32_t s1, uint32_t (&words)[WPL])
 {
 #pragma unroll
     for (int s = 0; s < WPL; ++s) words[s] = 0;
     const uint32_t nit = (s1 - s0 + 31) >> 5;
     const int2* __restrict__ xy = a.xy;
     uint32_t f = s0 + lane_id();
-    uint32_t shift, end;
-    interval_of(v, f, shift, end);
+    uint32_t r = 0, shift, end;
+    seek(tab, v.nint, f, r, shift, end);
     for (uint32_t it = 0; it < nit; it += 4, f += 128) {
         const bool full = s0 + (it + 4) * 32 <= s1;     // warp-uniform
         if (full && __all_sync(0xffffffffu, f + 96 < end)) {
@@ -354,7 +453,7 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
             for (int u = 0; u < 4; ++u) {
                 const uint32_t fu = f + 32u * u;
                 val[u] = fu < s1;
-                if (fu >= end) interval_of(v, fu, shift, end);
+                if (fu >= end) seek(tab, v.nint, fu, r, shift, end);
                 p[u] = val[u] ? __ldg(xy + (fu + shift)) : make_int2(0, 0);
             }
             uint32_t w[4];
@@ -369,17 +468,6 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     return c;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
-{
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if ((int)lane >= o) v += t;
-    }
-    return v;
 }
 
 // Warp-cooperative search: the query owning chunk g (largest q with base[q] <= g).
@@ -407,6 +495,8 @@ __device__ __forceinline__ uint64_t owner_query(const uint64_t* __restrict__ bas
 template <int WPL>
 __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 {
+    __shared__ WarpTab s_tab[kThreads / 32];
+    WarpTab* tab = &s_tab[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     // work items are chunks in processing order: wbase (curve order) or chunk_base (input order)
     const uint64_t* wb = a.wbase ? a.wbase : a.chunk_base;
@@ -419,16 +509,21 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
         if (g0 >= G) break;
         const uint64_t g1 = min(G, g0 + a.batch);
         uint64_t r = owner_query(wb, a.m, g0);
+        uint64_t loaded = ~0ull;
+        QView v;
         for (uint64_t w = g0; w < g1; ++w) {
             while (__ldg(wb + r + 1) <= w) ++r;
             const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
-            const QView v = load_query(a, q);
+            if (q != loaded) {   // consecutive chunks of one query share its table
+                v = load_query(a, q, tab);
+                loaded = q;
+            }
             const uint32_t j = (uint32_t)(w - __ldg(wb + r));
             const uint64_t g = a.perm ? __ldg(a.chunk_base + q) + j : w;   // mask slot
             const uint32_t s0 = j * a.chunk;
             const uint32_t s1 = min(v.S, s0 + a.chunk);
             uint32_t words[WPL];
-            const uint32_t cnt = filter_chunk<WPL>(a, v, s0, s1, words);
+            const uint32_t cnt = filter_chunk<WPL>(a, v, tab, s0, s1, words);
             if (g < a.mask_chunks) {
                 const uint32_t nw = (s1 - s0 + 31) >> 5;
                 uint32_t* mp = a.masks + g * W;
@@ -451,7 +546,9 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
 {
     // per-warp staging of the array positions of one group of 32 mask words (<= 1024 hits)
     __shared__ uint32_t s_pos[kThreads / 32][1024];
+    __shared__ WarpTab s_tab[kThreads / 32];
     uint32_t* buf = s_pos[threadIdx.x >> 5];
+    WarpTab* tab = &s_tab[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
         set_status(a.status, SFC_DEV_CAPACITY);
@@ -466,7 +563,8 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
             const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
             const uint32_t k = __ldg(a.counts + q);
             if (k == 0) continue;
-            const QView v = load_query(a, q);
+            const QView v = load_query(a, q, tab);
+            uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
             const uint64_t off = a.out_offsets[q];
             const uint64_t cb = __ldg(a.chunk_base + q);
             const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
@@ -485,7 +583,7 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                         words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
                     }
                 } else {
-                    filter_chunk<WPL>(a, v, s0, s1, words);
+                    filter_chunk<WPL>(a, v, tab, s0, s1, words);
                 }
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
@@ -499,15 +597,15 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                     uint32_t bits = wl;
                     const uint32_t fbase = s0 + ((uint32_t)(s * 32) + lane) * 32u;
                     if (bits) {
-                        // one interval lookup per word; a word that crosses an interval end
-                        // maps each bit separately
+                        // the lane's cursor moves to the word's interval; bits past its end
+                        // move it further
                         uint32_t shift, end;
-                        interval_of(v, fbase, shift, end);
-                        const bool one = fbase + 31 < end;
+                        seek(tab, v.nint, fbase, cr, shift, end);
                         while (bits) {
                             const uint32_t f = fbase + (uint32_t)(__ffs(bits) - 1);
                             bits &= bits - 1;
-                            buf[slot++] = one ? f + shift : map_pos(v, f);
+                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
+                            buf[slot++] = f + shift;
                         }
                     }
                     __syncwarp();
@@ -525,43 +623,6 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
             }
         }
     }
-}
-
-// ------------------------------------------------------------------------------------
-// ranges export (tests)
-// ------------------------------------------------------------------------------------
-template <class Bounds>
-__global__ void __launch_bounds__(kThreads) ranges_kernel(QueryArgs a, Bounds bounds_in, uint64_t* out_lo,
-                                                          uint64_t* out_hi, uint32_t* out_b,
-                                                          uint32_t* out_e, uint32_t* out_cnt)
-{
-    __shared__ HilbertTables tb;
-    __shared__ RootParams s_root;
-    Bounds bounds = bounds_in;
-    bounds.prepare(&s_root);
-    __syncthreads();
-    if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
-    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    const bool active = i < a.m;
-    int2 q = make_int2(0, 0);
-    int32_t delta = -1;
-    if (active) {
-        q = reinterpret_cast<const int2*>(a.q)[i];
-        delta = a.delta[i];
-    }
-    const bool ok = active && query_valid(q.x, q.y, delta);
-    QueryRanges R;
-    uint32_t b[4], e[4];
-    query_bounds(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, R, b, e);
-    if (!active) return;
-    for (int k = 0; k < 4; ++k) {
-        const bool u = k < R.cnt;
-        if (out_lo) out_lo[4 * i + k] = u ? R.lo[k] : 1;
-        if (out_hi) out_hi[4 * i + k] = u ? R.hi[k] : 0;
-        if (out_b) out_b[4 * i + k] = b[k];
-        if (out_e) out_e[4 * i + k] = e[k];
-    }
-    if (out_cnt) out_cnt[i] = (uint32_t)R.cnt;
 }
 
 __global__ void query_keys_kernel(const int32_t* __restrict__ q, uint64_t m, int curve, uint64_t* keys)
@@ -605,19 +666,34 @@ sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 
 }  // namespace
 
-sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st)
+template <int DROP, bool EXPORT>
+static void plan_dispatch(const QueryArgs& a, const LearnedModelView* lm, const PlanExport& ex, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
+    if (lm)
+        plan_kernel<LearnedBounds, DROP, EXPORT>
+            <<<g, kThreads, 0, st>>>(a, LearnedBounds{lm->root, lm->leaf, lm->stats}, ex);
+    else
+        plan_kernel<BinaryBounds, DROP, EXPORT><<<g, kThreads, 0, st>>>(a, BinaryBounds{}, ex);
+}
+
+template <bool EXPORT>
+static sfc_status plan_launch(const QueryArgs& a, const LearnedModelView* lm, const PlanExport& ex, cudaStream_t st)
 {
     if (a.m == 0) return SFC_OK;
-    const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
-    if (lm) {
-        LearnedBounds lb{lm->root, lm->leaf, lm->stats};
-        plan_kernel<LearnedBounds><<<g, kThreads, 0, st>>>(a, lb);
-    } else {
-        plan_kernel<BinaryBounds><<<g, kThreads, 0, st>>>(a, BinaryBounds{});
-    }
+    if (a.drop == 0) plan_dispatch<0, EXPORT>(a, lm, ex, st);
+    else if (a.drop == 1) plan_dispatch<1, EXPORT>(a, lm, ex, st);
+    else plan_dispatch<2, EXPORT>(a, lm, ex, st);
     count_launch();
     return launch_status();
 }
+
+sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st)
+{
+    return plan_launch<false>(a, lm, PlanExport{}, st);
+}
+
+int cover_intervals(int drop) { return drop == 0 ? Cover<0>::K : (drop == 1 ? Cover<1>::K : Cover<2>::K); }
 
 static unsigned flat_grid(uint64_t m)
 {
@@ -665,16 +741,11 @@ sfc_status launch_write(const QueryArgs& a, cudaStream_t st)
 sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_t* lo, uint64_t* hi,
                          uint32_t* b, uint32_t* e, uint32_t* cnt, cudaStream_t st)
 {
-    if (a.m == 0) return SFC_OK;
-    const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
-    if (lm) {
-        LearnedBounds lb{lm->root, lm->leaf, lm->stats};
-        ranges_kernel<LearnedBounds><<<g, kThreads, 0, st>>>(a, lb, lo, hi, b, e, cnt);
-    } else {
-        ranges_kernel<BinaryBounds><<<g, kThreads, 0, st>>>(a, BinaryBounds{}, lo, hi, b, e, cnt);
-    }
-    count_launch();
-    return launch_status();
+    QueryArgs x = a;
+    x.ranges = nullptr;
+    x.nchunks = nullptr;
+    x.scanned = nullptr;
+    return plan_launch<true>(x, lm, PlanExport{lo, hi, b, e, cnt}, st);
 }
 
 }  // namespace sfc

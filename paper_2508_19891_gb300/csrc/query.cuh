@@ -14,7 +14,9 @@ struct QueryArgs {
     const int32_t* q;            // [m][2]
     const int32_t* delta;        // [m]
     uint64_t m;
-    uint32_t* ranges;            // [m][8]: (begin, end) of up to four intervals
+    uint32_t* ranges;            // [m][2 * kint]: (begin, end) of up to kint intervals
+    uint32_t kint;               // intervals stored per query (4, 9 or 25 by the cover)
+    int drop;                    // cover refinement: 0 cells(Q), 1 or 2 levels finer
     uint32_t* nchunks;           // [m]
     uint64_t* chunk_base;        // [m + 1]
     uint32_t* counts;            // [m] hits per query
@@ -41,6 +43,7 @@ struct LearnedModelView {
 };
 
 sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st);
+int cover_intervals(int drop);   // intervals stored per query for a cover refinement
 sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
 // curve key of each query centre (invalid centres sort last) with the query index as value
 sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);

@@ -30,38 +30,79 @@ def assert_same(pts, qs, d, curve, dev, **opts):
 
 
 @pytest.mark.parametrize("curve", ["z", "h"])
-def test_ranges_and_bounds(cuda, curve):
+@pytest.mark.parametrize("cover", [0, 1, 2])
+def test_ranges_and_bounds(cuda, curve, cover):
     pts, qs, d = W.tiny_dense(11, 3000, 2000, 30, 1 << 26)
     d[:50] = 0
     d[50:60] = 1 << 29
     d[60:70] = 2 ** 31 - 1
-    qs[70:80] = [[0, 0], [(1 << 30) - 1, (1 << 30) - 1]] * 5
-    idx = sfc.sfc_build(to_dev(pts, cuda), curve)
+    d[70:90] = np.arange(1, 21)
+    qs[90:100] = [[0, 0], [(1 << 30) - 1, (1 << 30) - 1]] * 5
+    qs[100:110] = [[1 << 29, 5], [7, (1 << 30) - 2]] * 5
+    idx = sfc.sfc_build(to_dev(pts, cuda), curve, cover_refine=cover)
+    K = sfc.sfc_query_max_intervals(idx)
+    assert K == (2 ** cover + 1) ** 2 if cover else K == 4
     lo, hi, b, e, c = sfc.sfc_query_ranges(idx, to_dev(qs, cuda), to_dev(d, cuda))
     lo, hi, b, e, c = u64(lo), u64(hi), b.cpu().numpy(), e.cpu().numpy(), c.cpu().numpy()
     ref = oracle.build(pts, 30, curve)
     for i in range(len(qs)):
-        cells, _ = oracle.cells(int(qs[i, 0]), int(qs[i, 1]), int(d[i]), 30, curve)
+        if cover == 0:
+            cells, _ = oracle.cells(int(qs[i, 0]), int(qs[i, 1]), int(d[i]), 30, curve)
+        else:
+            cells = oracle.cells_refined(int(qs[i, 0]), int(qs[i, 1]), int(d[i]), 30, curve, cover)
         # the GPU merges intervals that abut in key order; the covered key set is the same
-        merged = []
-        for a, z in cells:
-            if merged and merged[-1][1] + 1 == a:
-                merged[-1] = (merged[-1][0], z)
-            else:
-                merged.append((a, z))
-        assert c[i] == len(merged) <= 4
+        merged = oracle.merge_abutting(cells)
+        assert c[i] == len(merged) <= K
         for r, (a, z) in enumerate(merged):
-            assert (int(lo[4 * i + r]), int(hi[4 * i + r])) == (a, z)
-            assert b[4 * i + r] == oracle.lower_bound(ref.keys, a)
-            assert e[4 * i + r] == oracle.lower_bound(ref.keys, z + 1)
+            assert (int(lo[K * i + r]), int(hi[K * i + r])) == (a, z)
+            assert b[K * i + r] == oracle.lower_bound(ref.keys, a)
+            assert e[K * i + r] == oracle.lower_bound(ref.keys, z + 1)
+        for r in range(len(merged), K):
+            assert (int(lo[K * i + r]), int(hi[K * i + r])) == (1, 0)
 
 
 @pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("cover", [0, 1, 2])
 @pytest.mark.parametrize("seed,side_bits,max_delta", [(1, 4, 6), (2, 6, 20), (3, 10, 300),
                                                        (4, 30, 1 << 27), (5, 16, 70000)])
-def test_tiny_vs_oracle(cuda, curve, seed, side_bits, max_delta):
+def test_tiny_vs_oracle(cuda, curve, cover, seed, side_bits, max_delta):
+    """Every cover reports the oracle's answer (Alg. 1 over cells(Q)) in the same order."""
     pts, qs, d = W.tiny_dense(seed, 5000, 3000, side_bits, max_delta)
-    assert_same(pts, qs, d, curve, cuda)
+    assert_same(pts, qs, d, curve, cuda, cover_refine=cover)
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("cover", [1, 2])
+def test_finer_cover_scans_less(cuda, curve, cover):
+    """A finer cover scans at most what cells(Q) scans (its cells lie inside cells(Q)'s), the
+    scanned total equals the oracle's per-query scan over its own intervals, and the answer,
+    with learned bounds too, is unchanged."""
+    wl = W.mixed_1e7(scale=0.01)
+    q, d = to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
+    scanned = {}
+    for cv in (0, cover):
+        idx, st = assert_same(wl.points, wl.queries, wl.delta, curve, cuda, cover_refine=cv,
+                              bounds="learned")
+        assert st == (0, 0)
+        scanned[cv] = sfc.sfc_query_stats(idx)["scanned"]
+    assert scanned[cover] <= scanned[0]
+    ref = oracle.build(wl.points, 30, curve)
+    want = 0
+    for i in range(wl.m):
+        for a, z in oracle.merge_abutting(oracle.cells_refined(int(wl.queries[i, 0]), int(wl.queries[i, 1]),
+                                                               int(wl.delta[i]), 30, curve, cover)):
+            want += oracle.lower_bound(ref.keys, z + 1) - oracle.lower_bound(ref.keys, a)
+    assert scanned[cover] == want
+
+
+@pytest.mark.parametrize("cover", [1, 2])
+def test_finer_cover_chunks_and_rescan(cuda, cover):
+    """Finer covers across chunk sizes and with the bitmask budget exhausted (the write pass
+    re-filters), where a chunk spans many short intervals."""
+    wl = W.mixed_1e7(scale=0.005)
+    for chunk in (32, 1024, 4096):
+        assert_same(wl.points, wl.queries, wl.delta, "h", cuda, cover_refine=cover, chunk=chunk)
+    assert_same(wl.points, wl.queries, wl.delta, "z", cuda, cover_refine=cover, mask_budget_mb=1)
 
 
 @pytest.mark.parametrize("curve", ["z", "h"])
@@ -186,17 +227,31 @@ def test_autotune(cuda):
     q, d = to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
     idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned")
     choice = sfc.sfc_autotune(idx, q, d, force=True)
-    assert choice["chunk"] in (256, 512, 1024, 2048, 4096)
+    assert choice["chunk"] in (256, 512, 1024, 2048, 4096) and choice["cover"] == 0
     assert choice["batch"] in (1, 2, 4, 8, 16) and choice["qbatch"] in (1, 2, 4, 8, 16)
     idx2 = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned")
     assert sfc.sfc_autotune(idx2, q, d) == choice          # served from the cache
     off, ids = sfc.query(idx2, q, d)
     roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta)
     assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+    # cover chosen by the tuner (cover_refine = -1), then set by hand
+    idx3 = sfc.sfc_build(to_dev(wl.points, cuda), "z", cover_refine=-1)
+    assert sfc.sfc_cover_refine(idx3) == 1
+    c3 = sfc.sfc_autotune(idx3, q, d, force=True)
+    assert c3["cover"] in (0, 1, 2) and sfc.sfc_cover_refine(idx3) == c3["cover"]
+    off, ids = sfc.query(idx3, q, d)
+    assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+    sfc.sfc_set_cover(idx3, 2)
+    assert sfc.sfc_query_max_intervals(idx3) == 25
+    off, ids = sfc.query(idx3, q, d)
+    assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+    with pytest.raises(sfc.SfcError):
+        sfc.sfc_set_cover(idx3, 3)
 
 
 @pytest.mark.parametrize("curve", ["z", "h"])
-def test_extreme_radii(cuda, curve):
+@pytest.mark.parametrize("cover", [0, 2])
+def test_extreme_radii(cuda, curve, cover):
     """Queries whose disc covers the whole domain (every point reported, the scan is the whole
     array and spans hundreds of chunks), radius 0 on stacked duplicates, and tiny queries in the
     same batch."""
@@ -207,7 +262,7 @@ def test_extreme_radii(cuda, curve):
                          pts[rng.integers(0, 200_000, 300)]])
     d = np.concatenate([np.array([2 ** 31 - 1, 1 << 30, 0, 3], np.int32),
                         rng.integers(0, 1 << 16, 300).astype(np.int32)])
-    idx, st = assert_same(pts, qs, d, curve, cuda)
+    idx, st = assert_same(pts, qs, d, curve, cuda, cover_refine=cover)
     off = oracle.query(oracle.build(pts, 30, curve), qs[:3], d[:3])[0]
     assert off[1] - off[0] == 200_000 and off[3] - off[2] == 500
     assert st == (0, 0)

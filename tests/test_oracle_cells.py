@@ -89,3 +89,42 @@ def test_level_values():
     assert oracle.level(8366) == 15    # 16732 <= 32768 < 33464
     assert oracle.level((1 << 28) + 1) == 30
     assert oracle.level(1 << 28) == 29
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("drop", [0, 1, 2])
+def test_refined_cells_exhaustive(curve, drop):
+    """Finer covers: every integer point of the closed ball is covered, every kept cell holds a
+    point of the ball, cells are disjoint, at most (2^drop + 1)^2 of them, all of side
+    2^max(0, l - drop)."""
+    w = 4
+    side = 1 << w
+    keys = _grid_keys(w, curve)
+    ys, xs = np.mgrid[0:side, 0:side]
+    for qy in range(0, side, 3):
+        for qx in range(0, side, 2):
+            for delta in range(0, side + 2):
+                rngs = oracle.cells_refined(qx, qy, delta, w, curve, drop)
+                l = max(0, oracle.level(delta, w) - drop)
+                assert len(rngs) <= (2 ** drop + 1) ** 2
+                inball = (xs - qx) ** 2 + (ys - qy) ** 2 <= delta * delta
+                kb = keys[inball]
+                cov = np.zeros(kb.shape, bool)
+                for lo, hi in rngs:
+                    assert hi - lo + 1 == 4 ** l and lo % (4 ** l) == 0
+                    cell = (keys >= lo) & (keys <= hi)
+                    assert (cell & inball).any()          # the cell meets the ball
+                    cov |= (kb >= lo) & (kb <= hi)
+                assert cov.all()                            # the ball is covered
+                for (a, b), (c, d) in zip(rngs, rngs[1:]):
+                    assert b < c
+
+
+def test_refined_drop0_is_subset_of_cells():
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        qx, qy = (int(v) for v in rng.integers(0, 1 << 30, 2))
+        delta = int(rng.integers(0, 1 << 22))
+        full, _ = oracle.cells(qx, qy, delta)
+        sub = oracle.cells_refined(qx, qy, delta, drop=0)
+        assert set(sub) <= set(full) and len(sub) >= 1
