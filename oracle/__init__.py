@@ -76,6 +76,10 @@ def _L():
         lib.oracle_cells.argtypes = [i32, i32, i32, c_int, c_int, P, P, P]
         lib.oracle_cells_refined.restype = c_int
         lib.oracle_cells_refined.argtypes = [i32, i32, i32, c_int, c_int, c_int, P, P, c_int]
+        lib.oracle_occupancy.restype = None
+        lib.oracle_occupancy.argtypes = [P, u64, c_int, c_int, P]
+        lib.oracle_cell_occupied.restype = c_int
+        lib.oracle_cell_occupied.argtypes = [P, c_int, c_int, c_int, u64]
         lib.oracle_query.restype = c_int
         lib.oracle_query.argtypes = [P, P, P, u64, P, P, u64, c_int, c_int, P, P, P, P, c_int]
         lib.oracle_brute.restype = c_int
@@ -170,6 +174,30 @@ def cells_refined(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z", drop:
     if cnt < 0:
         raise AssertionError("more cells than (2^drop + 1)^2")
     return [(int(lo[i]), int(hi[i])) for i in range(cnt)]
+
+
+def occupancy_words(D: int) -> int:
+    """32-bit words of the early-termination bitmap of depth D (all depths 0..D)."""
+    return ((4 ** (D + 1) - 1) // 3 + 31) // 32
+
+
+def occupancy(keys_arr: np.ndarray, D: int, w: int = OMEGA) -> np.ndarray:
+    """The early-termination quadtree's booleans (Sec. 2.2), one bit per node, depth after
+    depth (depth t from bit (4^t - 1) / 3)."""
+    k = _c(keys_arr, np.uint64)
+    out = np.empty(occupancy_words(D), np.uint32)
+    _L().oracle_occupancy(_ptr(k), k.shape[0], int(w), int(D), _ptr(out))
+    return out
+
+
+def occupancy_bit(bits: np.ndarray, t: int, v: int) -> int:
+    b = (4 ** t - 1) // 3 + int(v)
+    return int((int(bits[b // 32]) >> (b % 32)) & 1)
+
+
+def cell_occupied(bits: np.ndarray, D: int, l: int, lo: int, w: int = OMEGA) -> bool:
+    b = _c(bits, np.uint32)
+    return bool(_L().oracle_cell_occupied(_ptr(b), int(w), int(D), int(l), int(lo)))
 
 
 def merge_abutting(intervals):

@@ -395,3 +395,39 @@ int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t*
     free(tids);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Early-termination quadtree (Sec. 2.2, "Early termination").                           */
+/* ------------------------------------------------------------------------------------ */
+
+/* The boolean of every node of the complete quadtree of depth D over the bounding box G =
+ * [0, 2^w)^2: node v at depth t (0 <= t <= D) is the cell of level w - t whose label (the
+ * key prefix of Def. 2.3) is v; its boolean is true iff the cell contains a point.  Stored
+ * one bit per node, depth after depth: depth t starts at bit (4^t - 1) / 3, node v at that
+ * start + v.  Written as the definition: every point marks its cell on every level.
+ * `bits` must hold ((4^(D+1) - 1) / 3 + 31) / 32 words; it is cleared first. */
+void oracle_occupancy(const uint64_t* keys, uint64_t n, int w, int D, uint32_t* bits)
+{
+    const uint64_t total = (((uint64_t)1 << (2 * (D + 1))) - 1) / 3;
+    memset(bits, 0, ((total + 31) / 32) * sizeof(uint32_t));
+    for (uint64_t i = 0; i < n; ++i) {
+        for (int t = 0; t <= D; ++t) {
+            const uint64_t start = (((uint64_t)1 << (2 * t)) - 1) / 3;
+            const uint64_t v = keys[i] >> (2 * (w - t));
+            const uint64_t b = start + v;
+            bits[b / 32] |= 1u << (b % 32);
+        }
+    }
+}
+
+/* Whether the cell of level l whose key interval starts at `lo` may hold a point by the
+ * early-termination quadtree of depth D: the cell's own node when it is at depth <= D, else
+ * its ancestor at depth D (which only answers "empty" for the whole ancestor). */
+int oracle_cell_occupied(const uint32_t* bits, int w, int D, int l, uint64_t lo)
+{
+    int t = w - l;
+    if (t > D) t = D;
+    const uint64_t start = (((uint64_t)1 << (2 * t)) - 1) / 3;
+    const uint64_t b = start + (lo >> (2 * (w - t)));
+    return (int)((bits[b / 32] >> (b % 32)) & 1u);
+}
