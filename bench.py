@@ -45,11 +45,16 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
-    ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5"], default="mixed-1e7",
+    ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5", "normal-1e7"],
+                    default="mixed-1e7",
                     help="the headline is mixed-1e7; the others are supplementary measurements")
     ap.add_argument("--reorder", type=int, choices=[0, 1, 2], default=None,
                     help="query processing order (0 input, 1 curve, 2 automatic)")
     ap.add_argument("--leaves", type=int, default=None, help="leaf segments of the learned model")
+    ap.add_argument("--occupancy", type=int, default=0,
+                    help="early-termination quadtree depth (0 = off; the paper uses 12)")
+    ap.add_argument("--rel-side", type=float, default=1e-3,
+                    help="normal-1e7: query disc diameter relative to the domain side")
     ap.add_argument("--cover", type=int, choices=[-1, 0, 1, 2], default=-1,
                     help="cover of each query's ball: 0 cells(Q), 1/2 levels finer, -1 autotuned")
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
@@ -158,6 +163,8 @@ def run_ours(args, rank, world, local):
         opts["cover_refine"] = args.cover
     if args.leaves is not None:
         opts["leaves"] = args.leaves
+    if args.occupancy:
+        opts["occupancy_depth"] = args.occupancy
 
     # size the output once (the total is the same for every step) and let the autotuner pick
     # the scan's chunk size and work-queue batches for this shape (cached for later builds)
@@ -210,6 +217,7 @@ def run_ours(args, rank, world, local):
             c0, m0 = agg.get(name, (0, 0.0))
             agg[name] = (c0 + cnt, m0 + ms)
     stats = sfc.sfc_query_stats(profs[-1])
+    cell_stats = sfc.sfc_query_cell_stats(profs[-1])
     status, bits = sfc.sfc_device_status(profs[-1])
     for ix in profs:
         ix.close()
@@ -247,10 +255,11 @@ def run_ours(args, rank, world, local):
             "reported_pts_per_s": world * stats["hits"] / (ms_per_step / 1e3),
             "hits_per_step": stats["hits"], "scanned_per_step": S, "chunks": stats["chunks"],
             "scan_amplification": S / max(stats["hits"], 1),
+            "cover_cells": cell_stats["cells"], "cells_found_empty": cell_stats["empty"],
         },
     }
     if rank == 0 and not args.no_extras:
-        bopts = {"cover_refine": tuned["cover"]}
+        bopts = {"cover_refine": tuned["cover"], "occupancy_depth": args.occupancy}
         if args.leaves is not None:
             bopts["leaves"] = args.leaves
         out["breakdown"].update(extras(sfc, torch, pts, q, d, total, n, m, flush, bopts))
@@ -289,6 +298,10 @@ def make_workload(args, rank):
         return workloads.mixed_1e8(scale=args.scale, seed=4 + 7919 * rank)
     if args.workload == "uniform-1e5":
         return workloads.uniform_1e5(scale=args.scale, seed=1 + 7919 * rank)
+    if args.workload == "normal-1e7":
+        return workloads.normal_uniform_queries(max(2, int(10_000_000 * args.scale)),
+                                                max(1, int(1_000_000 * args.scale)), args.rel_side,
+                                                seed=6 + 7919 * rank)
     return workloads.mixed_1e7(scale=args.scale, seed=instance_seed(rank))
 
 
@@ -479,7 +492,7 @@ def cpu_baseline(wl, budget_s: float):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = workloads.mixed_1e7(scale=args.scale, seed=instance_seed(0))
+    wl = make_workload(args, 0)
     threads = os.cpu_count() or 1
     vals = []
     det = None
@@ -492,7 +505,7 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "n": wl.n, "m": wl.m, "curve": "z",
+           "data": "synthetic", "config": {"workload": args.workload, "n": wl.n, "m": wl.m, "curve": "z",
                                            "bounds": "binary (std lower_bound)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": (f"per step: oracle build of all {wl.n} points + the first "

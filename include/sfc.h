@@ -85,6 +85,12 @@ typedef struct {
                                l - 2 (at most 9 or 25) that hold an integer point of the closed
                                ball, so fewer points are scanned for more key intervals; -1 the
                                choice of sfc_autotune (1 until it runs) (default 0) */
+    int occupancy_depth;    /* early termination (Sec. 2.2): depth D of a quadtree over the
+                               domain with one bit per node (the cell holds a point), built
+                               with the index and after every sfc_update; queries drop the
+                               cells of their cover that it shows empty (a cell deeper than D
+                               answers for its depth-D ancestor).  0 = off, 1..13; D = 12 (the
+                               paper's) takes 2.8 MB (default 0) */
 } sfc_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -208,6 +214,18 @@ sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);
  * cover it was captured with; reserve (sfc_reserve_queries) after a change to a finer cover,
  * since the per-query interval table grows with it. */
 sfc_status sfc_set_cover(sfc_index* idx, int refine);
+
+/* Copies the early-termination bitmap (opt->occupancy_depth > 0): node v of depth t (the cell
+ * of level 30 - t whose key prefix, Def. 2.3, is v) is bit (4^t - 1) / 3 + v, bit b in word
+ * b / 32 at position b % 32; ((4^(D+1) - 1) / 3 + 31) / 32 words in all.  d_out uint32[words]
+ * in device memory; *h_depth receives D.  SFC_ERR_STATE when the index has no bitmap,
+ * SFC_ERR_CAPACITY when words is too small (nothing copied). */
+sfc_status sfc_get_occupancy(const sfc_index* idx, uint32_t* d_out, uint64_t words, int* h_depth,
+                             void* stream);
+
+/* Cover statistics of the last query batch: *h_cells the cells of all covers, *h_empty those
+ * dropped as empty by the early-termination bitmap.  Synchronises `stream`. */
+sfc_status sfc_query_cell_stats(const sfc_index* idx, uint64_t* h_cells, uint64_t* h_empty, void* stream);
 
 /* The cover currently used by queries (0, 1 or 2), or -1 for idx == NULL. */
 int sfc_cover_refine(const sfc_index* idx);

@@ -49,7 +49,7 @@ class sfc_options(ctypes.Structure):
                 ("train_samples", ctypes.c_int), ("learning_rate", ctypes.c_float),
                 ("chunk", ctypes.c_int), ("mask_budget_mb", ctypes.c_int),
                 ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int), ("root", ctypes.c_int),
-                ("cover_refine", ctypes.c_int)]
+                ("cover_refine", ctypes.c_int), ("occupancy_depth", ctypes.c_int)]
 
 
 class sfc_profile_entry(ctypes.Structure):
@@ -87,6 +87,8 @@ def lib():
             "sfc_reserve_queries": (ci, [P, u64, P]),
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_set_cover": (ci, [P, ci]),
+            "sfc_get_occupancy": (ci, [P, P, u64, P, P]),
+            "sfc_query_cell_stats": (ci, [P, P, P, P]),
             "sfc_cover_refine": (ci, [P]),
             "sfc_query_max_intervals": (ci, [P]),
             "sfc_train_model": (ci, [P, P]),
@@ -387,6 +389,23 @@ def sfc_reserve_queries(index: Index, m: int, stream=None):
 
 def sfc_set_bounds_mode(index: Index, mode):
     _check(lib().sfc_set_bounds_mode(index.handle, _bounds(mode)), "sfc_set_bounds_mode")
+
+
+def sfc_get_occupancy(index: Index, depth: int, stream=None) -> torch.Tensor:
+    """The early-termination bitmap as int32 words (bit layout in include/sfc.h)."""
+    words = ((4 ** (depth + 1) - 1) // 3 + 31) // 32
+    out = torch.empty(words, dtype=torch.int32, device=index.device)
+    d = ctypes.c_int()
+    _check(lib().sfc_get_occupancy(index.handle, _dptr(out), words, ctypes.byref(d), _stream(stream)),
+           "sfc_get_occupancy")
+    return out
+
+
+def sfc_query_cell_stats(index: Index, stream=None) -> dict:
+    c, e = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().sfc_query_cell_stats(index.handle, ctypes.byref(c), ctypes.byref(e), _stream(stream)),
+           "sfc_query_cell_stats")
+    return {"cells": c.value, "empty": e.value}
 
 
 def sfc_set_cover(index: Index, refine: int):

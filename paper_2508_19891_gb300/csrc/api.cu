@@ -84,7 +84,8 @@ sfc_status ensure_status_buf(sfc_index* idx, cudaStream_t st)
 
 uint32_t* status_word(sfc_index* idx) { return idx->status.as<uint32_t>(); }
 // status buffer: u32 status word, padding, then u64 counters [0..2] learned-bounds
-// statistics, [3] points scanned by the last batch
+// statistics, [3] points scanned by the last batch, [4] cover cells, [5] of them found empty
+// by the early-termination bitmap
 unsigned long long* model_stats(sfc_index* idx)
 {
     return reinterpret_cast<unsigned long long*>(idx->status.as<unsigned char>() + 16);
@@ -109,6 +110,10 @@ sfc_status build_from_device(sfc_index* idx, const int32_t* d_points, cudaStream
         ProfScope ps(idx, "sort", st);
         SFC_TRY(radix_sort(src, n, dst, idx->sort_ws, status_word(idx), st));
     }
+    if (idx->opt.occupancy_depth > 0) {
+        ProfScope ps(idx, "occupancy", st);
+        SFC_TRY(build_occupancy(idx, st));
+    }
     // the id -> coordinates table of the dynamic setting starts as a copy of the input
     SFC_TRY(idx->xy_by_id.ensure(n * sizeof(int2), st));
     if (n) SFC_CUDA_TRY(cudaMemcpyAsync(idx->xy_by_id.ptr, d_points, n * sizeof(int2),
@@ -132,6 +137,11 @@ QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint
     a.status = status_word(idx);
     a.drop = idx->drop;
     a.kint = (uint32_t)cover_intervals(idx->drop);
+    if (idx->opt.occupancy_depth > 0 && idx->occ.ptr) {
+        a.occ = idx->occ.as<uint32_t>();
+        a.occ_depth = idx->opt.occupancy_depth;
+    }
+    a.cells = model_stats(idx) + 4;
     return a;
 }
 
@@ -203,7 +213,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.out_offsets = d_out_offsets;
     a.scanned = scan_stats(idx);
     // per-batch statistics: learned-bounds counters and the scanned total
-    SFC_CUDA_TRY(cudaMemsetAsync(model_stats(idx), 0, 4 * sizeof(unsigned long long), st));
+    SFC_CUDA_TRY(cudaMemsetAsync(model_stats(idx), 0, 6 * sizeof(unsigned long long), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.counts, 0, m * sizeof(uint32_t), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, 4 * sizeof(unsigned long long), st));
     LearnedModelView lv;
@@ -301,6 +311,7 @@ void sfc_default_options(sfc_options* opt)
     opt->profile = 0;
     opt->root = SFC_ROOT_PWL;
     opt->cover_refine = 0;
+    opt->occupancy_depth = 0;
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
@@ -316,7 +327,8 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     if (o.leaves < 1 || o.leaves > (1 << 20) || o.mask_budget_mb < 1 || o.train_samples < 2 ||
         o.train_steps < 0 || o.reorder_queries < 0 || o.reorder_queries > 2 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
         (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED) ||
-        (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP) || o.cover_refine < -1 || o.cover_refine > 2)
+        (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP) || o.cover_refine < -1 || o.cover_refine > 2 ||
+        o.occupancy_depth < 0 || o.occupancy_depth > 13)
         return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     sfc_index* idx = new (std::nothrow) sfc_index();
@@ -402,6 +414,8 @@ sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* str
     SFC_TRY(idx->xy.ensure(n1 * sizeof(int2), st));
     SFC_TRY(idx->xy_by_id.ensure(n1 * sizeof(int2), st));
     SFC_TRY(ensure_alive_bits(idx, n1, st));
+    if (idx->opt.occupancy_depth > 0)
+        SFC_TRY(idx->occ.ensure(occupancy_words(idx->opt.occupancy_depth) * sizeof(uint32_t), st));
     SFC_TRY(reserve_sort(idx->sort_ws, n1, st));
     SFC_TRY(ensure_query_ws(idx, m_max, st));
     SFC_TRY(reserve_scan(idx->scan_ws, std::max<uint64_t>(m_max, n1) + 1, st));
@@ -653,6 +667,33 @@ sfc_status sfc_set_cover(sfc_index* idx, int refine)
 {
     if (!idx || refine < 0 || refine > 2) return SFC_ERR_INVALID;
     idx->drop = refine;
+    return SFC_OK;
+}
+
+sfc_status sfc_get_occupancy(const sfc_index* cidx, uint32_t* d_out, uint64_t words, int* h_depth, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx || !d_out) return SFC_ERR_INVALID;
+    const int D = idx->opt.occupancy_depth;
+    if (D <= 0 || !idx->occ.ptr) return SFC_ERR_STATE;
+    const uint64_t need = occupancy_words(D);
+    if (words < need) return SFC_ERR_CAPACITY;
+    if (h_depth) *h_depth = D;
+    SFC_CUDA_TRY(cudaMemcpyAsync(d_out, idx->occ.ptr, need * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                 as_stream(stream)));
+    return SFC_OK;
+}
+
+sfc_status sfc_query_cell_stats(const sfc_index* cidx, uint64_t* h_cells, uint64_t* h_empty, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx || !idx->status.ptr) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    unsigned long long v[2] = {0, 0};
+    SFC_CUDA_TRY(cudaMemcpyAsync(v, model_stats(idx) + 4, sizeof(v), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_cells) *h_cells = v[0];
+    if (h_empty) *h_empty = v[1];
     return SFC_OK;
 }
 

@@ -75,6 +75,7 @@ struct sfc_index {
     sfc::DevBuf xy_by_id;               // coordinates by id (dynamic setting)
     sfc::DevBuf alive;                  // liveness bitmap by id
     sfc::DevBuf status;                 // device status word + model statistics
+    sfc::DevBuf occ;                    // early-termination bitmap (occupancy_depth > 0)
 
     sfc::SortWorkspace sort_ws;
     sfc::ScanWorkspace scan_ws;
@@ -96,6 +97,9 @@ sfc_status refit_model(sfc_index* idx, int steps, cudaStream_t st);
 sfc_status apply_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins, const uint32_t* d_del,
                         uint64_t k_del, uint32_t* h_first, cudaStream_t st);
 const RootParams* model_root_device(sfc_index* idx);
+// early-termination bitmap of the sorted keys (no-op when opt.occupancy_depth == 0)
+sfc_status build_occupancy(sfc_index* idx, cudaStream_t st);
+uint64_t occupancy_words(int depth);
 
 // Records CUDA events around a step when profiling is on.
 class ProfScope {

@@ -166,14 +166,27 @@ struct Cover {
     static constexpr int K = NX * NX;   // 4, 9, 25 interval slots per query
 };
 
+// Early termination (Sec. 2.2): whether the cell of level l whose key interval starts at c may
+// hold a point -- the bit of its own node when the node is within depth D, else of its
+// ancestor at depth D.
+__device__ __forceinline__ bool cell_occupied(const uint32_t* __restrict__ occ, int D, int l, uint64_t c)
+{
+    const int t = min(kOmega - l, D);
+    const uint64_t b = occupancy_level_start(t) + (c >> (2 * (kOmega - t)));
+    return (__ldg(occ + (b >> 5)) >> (b & 31)) & 1u;
+}
+
 // Writes the cover's key intervals to lo/hi (sorted, abutting ones merged); returns how many.
 // DROP 0: cells(Q), the cells of level l (2 delta <= 2^l < 4 delta, capped at omega) that meet
 // the clipped square Q.  DROP > 0: the cells of level max(0, l - DROP) that hold an integer
 // point of the closed ball (the distance from q to the cell's nearest integer point is at most
-// delta).  Each cell gives the key interval [pi(C)o0, pi(C)o1] (Observation).
+// delta).  Each cell gives the key interval [pi(C)o0, pi(C)o1] (Observation).  With the
+// early-termination bitmap (occ != NULL), cells it shows empty are dropped; ncell / nempty
+// count the cover's cells and the dropped ones.
 template <int DROP>
 __device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb, int32_t qx, int32_t qy,
-                                             int32_t delta, uint64_t* lo, uint64_t* hi)
+                                             int32_t delta, const uint32_t* occ, int D, uint64_t* lo,
+                                             uint64_t* hi, uint32_t& ncell, uint32_t& nempty)
 {
     constexpr int K = Cover<DROP>::K;
     const int64_t d = delta;
@@ -198,6 +211,11 @@ __device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb,
             }
             if (cnt == K) break;   // unreachable: at most Cover<DROP>::NX cells per axis
             const uint64_t c = curve_key(curve, tb, (uint32_t)(cx << l), (uint32_t)(cy << l)) & ~span;
+            ++ncell;
+            if (occ && !cell_occupied(occ, D, l, c)) {
+                ++nempty;
+                continue;
+            }
             int j = cnt;
             while (j > 0 && lo[j - 1] > c) { lo[j] = lo[j - 1]; hi[j] = hi[j - 1]; --j; }
             lo[j] = c;
@@ -223,14 +241,16 @@ __device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb,
 // bounds b[r], e[r]; returns their number.  Endpoints go through the bound search in lock-step
 // batches of 8 (eight independent searches in flight per thread).
 template <class Bounds, int DROP>
-__device__ __forceinline__ int query_bounds(const Bounds& bounds, int curve, const HilbertTables* tb,
-                                            const uint64_t* keys, uint32_t n, bool ok, int32_t qx,
-                                            int32_t qy, int32_t delta, uint64_t* lo, uint64_t* hi,
-                                            uint32_t* b, uint32_t* e, BoundStats& bs)
+__device__ __forceinline__ int query_bounds(const Bounds& bounds, const QueryArgs& a, const HilbertTables* tb,
+                                            int32_t qx, int32_t qy, int32_t delta, uint64_t* lo, uint64_t* hi,
+                                            uint32_t* b, uint32_t* e, BoundStats& bs, uint32_t& ncell,
+                                            uint32_t& nempty)
 {
     constexpr int K = Cover<DROP>::K;
     constexpr int NB = (2 * K + 7) / 8;
-    const int cnt = ok ? derive_ranges<DROP>(curve, tb, qx, qy, delta, lo, hi) : 0;
+    const uint64_t* keys = a.keys;
+    const uint32_t n = a.n;
+    const int cnt = derive_ranges<DROP>(a.curve, tb, qx, qy, delta, a.occ, a.occ_depth, lo, hi, ncell, nempty);
     const int ne = 2 * cnt;
 #pragma unroll 1
     for (int bi = 0; bi < NB && 8 * bi < ne; ++bi) {
@@ -288,8 +308,8 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
     uint64_t lo[K], hi[K];
     uint32_t b[K], e[K];
     BoundStats bs;
-    const int cnt = ok ? query_bounds<Bounds, DROP>(bounds, a.curve, &tb, a.keys, a.n, ok, q.x, q.y, delta, lo,
-                                                    hi, b, e, bs)
+    uint32_t ncell = 0, nempty = 0;
+    const int cnt = ok ? query_bounds<Bounds, DROP>(bounds, a, &tb, q.x, q.y, delta, lo, hi, b, e, bs, ncell, nempty)
                        : 0;
     uint64_t S = 0;
     for (int k = 0; k < cnt; ++k) S += e[k] - b[k];
@@ -298,6 +318,13 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
     if (a.scanned) {
         const unsigned long long t = warp_sum_u64(S);
         if (lane_id() == 0 && t) atomicAdd(a.scanned, t);
+    }
+    if (a.cells) {
+        const unsigned long long tc = warp_sum_u64(ncell), te = warp_sum_u64(nempty);
+        if (lane_id() == 0 && tc) {
+            atomicAdd(a.cells, tc);
+            if (te) atomicAdd(a.cells + 1, te);
+        }
     }
     if constexpr (Bounds::kStats) {
         if (bounds.stats) {
@@ -745,6 +772,7 @@ sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_
     x.ranges = nullptr;
     x.nchunks = nullptr;
     x.scanned = nullptr;
+    x.cells = nullptr;
     return plan_launch<true>(x, lm, PlanExport{lo, hi, b, e, cnt}, st);
 }
 

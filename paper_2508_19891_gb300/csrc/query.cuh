@@ -34,6 +34,10 @@ struct QueryArgs {
     // optional processing order: queries handed out in curve order of their centres
     const uint32_t* perm;        // [m] query index at each processing rank (NULL: identity)
     const uint64_t* wbase;       // [m + 1] chunk bases in processing order (NULL: chunk_base)
+    // early-termination bitmap (NULL: off) and the cover statistics
+    const uint32_t* occ;
+    int occ_depth;
+    unsigned long long* cells;   // [0] cells of the covers, [1] of them found empty
 };
 
 struct LearnedModelView {

@@ -185,11 +185,14 @@ void release_index(sfc_index* idx, cudaStream_t st)
     idx->xy_by_id.release(st);
     idx->alive.release(st);
     idx->status.release(st);
+    idx->occ.release(st);
     release_sort_ws(idx->sort_ws, st);
     idx->scan_ws.flags.release(st);
     QueryWs& q = idx->qws;
     q.ranges.release(st); q.nchunks.release(st); q.chunk_base.release(st);
     q.counts.release(st); q.masks.release(st); q.ctr.release(st);
+    q.qkeys.release(st); q.qkeys_sorted.release(st); q.perm.release(st);
+    q.nch_sorted.release(st); q.wbase.release(st);
     HostStage& h = idx->stage;
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
     ModelState& M = idx->model;
@@ -339,6 +342,7 @@ sfc_status apply_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins
     idx->next_id = next_id + (uint32_t)k_ins;
     if (h_first) *h_first = next_id;
     idx->qws.pending.valid = false;
+    SFC_TRY(build_occupancy(idx, st));
     if (idx->model.trained) {
         const int steps = std::max(20, idx->opt.train_steps / 5);
         SFC_TRY(refit_model(idx, steps, st));
