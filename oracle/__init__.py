@@ -33,6 +33,18 @@ CURVE_HILBERT = 1
 OMEGA = 30  # bits per coordinate on the GPU path
 
 
+NORM_DISC = 0     # closed disc dx^2 + dy^2 <= delta^2 (problem statement)
+NORM_SQUARE = 1   # closed square max(|dx|, |dy|) <= delta (the experiments' windows)
+
+
+def norm_id(norm) -> int:
+    if norm in (NORM_DISC, "disc", "l2"):
+        return NORM_DISC
+    if norm in (NORM_SQUARE, "square", "box", "linf"):
+        return NORM_SQUARE
+    raise ValueError(f"unknown norm {norm!r}")
+
+
 def curve_id(curve) -> int:
     if curve in (CURVE_Z, "z", "Z", "morton"):
         return CURVE_Z
@@ -80,6 +92,12 @@ def _L():
         lib.oracle_occupancy.argtypes = [P, u64, c_int, c_int, P]
         lib.oracle_cell_occupied.restype = c_int
         lib.oracle_cell_occupied.argtypes = [P, c_int, c_int, c_int, u64]
+        lib.oracle_query_norm.restype = c_int
+        lib.oracle_query_norm.argtypes = [P, P, P, u64, P, P, u64, c_int, c_int, c_int, P, P, P, P, c_int]
+        lib.oracle_brute_norm.restype = c_int
+        lib.oracle_brute_norm.argtypes = [P, u64, P, P, u64, c_int, c_int, P, P, P, c_int]
+        lib.oracle_cells_refined_norm.restype = c_int
+        lib.oracle_cells_refined_norm.argtypes = [i32, i32, i32, c_int, c_int, c_int, c_int, P, P, c_int]
         lib.oracle_query.restype = c_int
         lib.oracle_query.argtypes = [P, P, P, u64, P, P, u64, c_int, c_int, P, P, P, P, c_int]
         lib.oracle_brute.restype = c_int
@@ -163,14 +181,14 @@ def cells(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z"):
     return [(int(lo[i]), int(hi[i])) for i in range(cnt)], int(lv.value)
 
 
-def cells_refined(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z", drop: int = 1):
+def cells_refined(qx: int, qy: int, delta: int, w: int = OMEGA, curve="z", drop: int = 1, norm="disc"):
     """Key intervals of the cells one (or `drop`) quadtree levels below cells(Q) that contain
-    an integer point of the closed ball, sorted by lo (not merged)."""
+    an integer point of the closed window (disc or square), sorted by lo (not merged)."""
     maxc = (2 ** drop + 1) ** 2
     lo = np.zeros(maxc, np.uint64)
     hi = np.zeros(maxc, np.uint64)
-    cnt = _L().oracle_cells_refined(int(qx), int(qy), int(delta), int(w), curve_id(curve), int(drop),
-                                    _ptr(lo), _ptr(hi), maxc)
+    cnt = _L().oracle_cells_refined_norm(int(qx), int(qy), int(delta), int(w), curve_id(curve), int(drop),
+                                         norm_id(norm), _ptr(lo), _ptr(hi), maxc)
     if cnt < 0:
         raise AssertionError("more cells than (2^drop + 1)^2")
     return [(int(lo[i]), int(hi[i])) for i in range(cnt)]
@@ -210,9 +228,11 @@ def merge_abutting(intervals):
     return out
 
 
-def query(index: Index, q: np.ndarray, delta: np.ndarray, threads: int = 1, want_scanned=False):
+def query(index: Index, q: np.ndarray, delta: np.ndarray, threads: int = 1, want_scanned=False,
+          norm="disc"):
     """Alg. 1 for every query.  Returns (offsets u64[m+1], ids u32[offsets[m]]) with each
-    query's ids in ascending (key, id) order, plus the scanned counts if asked."""
+    query's ids in ascending (key, id) order, plus the scanned counts if asked.  norm: the
+    closed disc of radius delta (default) or the closed square of half-side delta."""
     q = _c(q, np.int32).reshape(-1, 2)
     delta = _c(delta, np.int32).reshape(-1)
     m = q.shape[0]
@@ -220,21 +240,23 @@ def query(index: Index, q: np.ndarray, delta: np.ndarray, threads: int = 1, want
     counts = np.empty(m, np.uint64)
     scanned = np.empty(m, np.uint64)
     L = _L()
-    L.oracle_query(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q),
-                   _ptr(delta), m, index.w, index.curve, _ptr(counts), None, None,
-                   _ptr(scanned), int(threads))
+    nm = norm_id(norm)
+    L.oracle_query_norm(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q),
+                        _ptr(delta), m, index.w, index.curve, nm, _ptr(counts), None, None,
+                        _ptr(scanned), int(threads))
     offsets = np.zeros(m + 1, np.uint64)
     np.cumsum(counts, out=offsets[1:])
     ids = np.empty(int(offsets[m]), np.uint32)
-    L.oracle_query(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q),
-                   _ptr(delta), m, index.w, index.curve, None, _ptr(offsets), _ptr(ids),
-                   None, int(threads))
+    L.oracle_query_norm(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q),
+                        _ptr(delta), m, index.w, index.curve, nm, None, _ptr(offsets), _ptr(ids),
+                        None, int(threads))
     if want_scanned:
         return offsets, ids, scanned
     return offsets, ids
 
 
-def brute(xy: np.ndarray, q: np.ndarray, delta: np.ndarray, w: int = OMEGA, threads: int = 1):
+def brute(xy: np.ndarray, q: np.ndarray, delta: np.ndarray, w: int = OMEGA, threads: int = 1,
+          norm="disc"):
     """O(n*m) reporting straight from the problem statement; ids ascending per query."""
     xy = _c(xy, np.int32).reshape(-1, 2)
     q = _c(q, np.int32).reshape(-1, 2)
@@ -242,13 +264,14 @@ def brute(xy: np.ndarray, q: np.ndarray, delta: np.ndarray, w: int = OMEGA, thre
     m = q.shape[0]
     counts = np.empty(m, np.uint64)
     L = _L()
-    L.oracle_brute(_ptr(xy), xy.shape[0], _ptr(q), _ptr(delta), m, int(w), _ptr(counts), None,
-                   None, int(threads))
+    nm = norm_id(norm)
+    L.oracle_brute_norm(_ptr(xy), xy.shape[0], _ptr(q), _ptr(delta), m, int(w), nm, _ptr(counts), None,
+                        None, int(threads))
     offsets = np.zeros(m + 1, np.uint64)
     np.cumsum(counts, out=offsets[1:])
     ids = np.empty(int(offsets[m]), np.uint32)
-    L.oracle_brute(_ptr(xy), xy.shape[0], _ptr(q), _ptr(delta), m, int(w), None, _ptr(offsets),
-                   _ptr(ids), int(threads))
+    L.oracle_brute_norm(_ptr(xy), xy.shape[0], _ptr(q), _ptr(delta), m, int(w), nm, None, _ptr(offsets),
+                        _ptr(ids), int(threads))
     return offsets, ids
 
 

@@ -199,13 +199,25 @@ int oracle_cells(int32_t qx, int32_t qy, int32_t delta, int w, int curve,
     return cnt;
 }
 
+/* The query's window: the closed disc dx^2 + dy^2 <= delta^2 of the problem statement (norm 0),
+ * or the closed square max(|dx|, |dy|) <= delta (norm 1), the axis-parallel window of side
+ * 2 delta + 1 points that the experiments of Sec. 3 query (their windows are squares; the
+ * result sizes printed in App. B match a square, not a disc). */
+static int in_window(int64_t dx, int64_t dy, int64_t delta, int norm)
+{
+    if (norm == 1) return (dx < 0 ? -dx : dx) <= delta && (dy < 0 ? -dy : dy) <= delta;
+    return dx * dx + dy * dy <= delta * delta;
+}
+
 /* Refined cover (a finer quadtree level than cells(Q), Sec. 2 "Efficiency" notes the cover's
  * volume can be 2 * 2^d times that of Q): the cells at level l' = max(0, l - drop), where l is
  * the level of cells(Q), that contain at least one integer point of the closed ball
- * B_delta(q) within the domain; returns how many (at most (2^drop + 1)^2), key intervals
- * sorted by lo, not merged.  drop = 0 keeps only cells(Q)'s cells that meet the ball. */
-int oracle_cells_refined(int32_t qx, int32_t qy, int32_t delta, int w, int curve, int drop,
-                         uint64_t* lo, uint64_t* hi, int maxc)
+ * B_delta(q) within the domain -- of the window of `norm` (in_window): for the square window
+ * every cell meeting the clipped square Q qualifies; returns how many (at most
+ * (2^drop + 1)^2), key intervals sorted by lo, not merged.  drop = 0 keeps only cells(Q)'s
+ * cells that meet the window. */
+int oracle_cells_refined_norm(int32_t qx, int32_t qy, int32_t delta, int w, int curve, int drop, int norm,
+                              uint64_t* lo, uint64_t* hi, int maxc)
 {
     int64_t side = (int64_t)1 << w;
     int64_t d = delta;
@@ -226,7 +238,7 @@ int oracle_cells_refined(int32_t qx, int32_t qy, int32_t delta, int w, int curve
             int64_t dx = 0, dy = 0;
             if (qx < ax0) dx = ax0 - qx; else if (qx > ax1) dx = qx - ax1;
             if (qy < ay0) dy = ay0 - qy; else if (qy > ay1) dy = qy - ay1;
-            if (dx * dx + dy * dy > d * d) continue;
+            if (!in_window(dx, dy, d, norm)) continue;
             if (cnt == maxc) return -1;
             uint64_t corner = oracle_key((uint32_t)(cx << l), (uint32_t)(cy << l), w, curve);
             uint64_t span = ((uint64_t)1 << (2 * l)) - 1;
@@ -242,6 +254,12 @@ int oracle_cells_refined(int32_t qx, int32_t qy, int32_t delta, int w, int curve
         lo[j + 1] = a; hi[j + 1] = b;
     }
     return cnt;
+}
+
+int oracle_cells_refined(int32_t qx, int32_t qy, int32_t delta, int w, int curve, int drop,
+                         uint64_t* lo, uint64_t* hi, int maxc)
+{
+    return oracle_cells_refined_norm(qx, qy, delta, w, curve, drop, 0, lo, hi, maxc);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -260,19 +278,18 @@ static int query_valid(int32_t qx, int32_t qy, int32_t delta, int w)
  * scanned (if not NULL) receives the number of array entries visited. */
 static uint64_t query_one(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy,
                           uint64_t n, int32_t qx, int32_t qy, int32_t delta, int w, int curve,
-                          uint32_t* out, uint64_t* scanned)
+                          int norm, uint32_t* out, uint64_t* scanned)
 {
     if (!query_valid(qx, qy, delta, w)) { if (scanned) *scanned = 0; return 0; }
     uint64_t lo[4], hi[4];
     int cnt = oracle_cells(qx, qy, delta, w, curve, lo, hi, NULL);
-    int64_t d2 = (int64_t)delta * (int64_t)delta;
     uint64_t k = 0, s = 0;
     for (int c = 0; c < cnt; ++c) {
         uint64_t x = oracle_lower_bound(skeys, n, lo[c]);
         while (x < n && skeys[x] <= hi[c]) {
             int64_t dx = (int64_t)sxy[2 * x] - qx;
             int64_t dy = (int64_t)sxy[2 * x + 1] - qy;
-            if (dx * dx + dy * dy <= d2) {
+            if (in_window(dx, dy, delta, norm)) {
                 if (out) out[k] = sids[x];
                 ++k;
             }
@@ -286,7 +303,7 @@ static uint64_t query_one(const uint64_t* skeys, const uint32_t* sids, const int
 
 typedef struct {
     const uint64_t* skeys; const uint32_t* sids; const int32_t* sxy; uint64_t n;
-    const int32_t* q; const int32_t* delta; uint64_t m0, m1; int w, curve;
+    const int32_t* q; const int32_t* delta; uint64_t m0, m1; int w, curve, norm;
     uint64_t* counts; const uint64_t* offsets; uint32_t* out_ids; uint64_t* scanned;
 } query_job;
 
@@ -297,7 +314,7 @@ static void* query_worker(void* arg)
         uint32_t* out = j->out_ids ? j->out_ids + j->offsets[i] : NULL;
         uint64_t s = 0;
         uint64_t k = query_one(j->skeys, j->sids, j->sxy, j->n, j->q[2 * i], j->q[2 * i + 1],
-                               j->delta[i], j->w, j->curve, out, &s);
+                               j->delta[i], j->w, j->curve, j->norm, out, &s);
         if (j->counts) j->counts[i] = k;
         if (j->scanned) j->scanned[i] = s;
     }
@@ -308,10 +325,10 @@ static void* query_worker(void* arg)
  * queries.  With out_ids == NULL only counts (and scanned) are produced; otherwise the ids of
  * query i are written at out_ids[offsets[i] ...].  Queries are independent, so the split
  * does not change any result. */
-int oracle_query(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy, uint64_t n,
-                 const int32_t* q, const int32_t* delta, uint64_t m, int w, int curve,
-                 uint64_t* counts, const uint64_t* offsets, uint32_t* out_ids,
-                 uint64_t* scanned, int threads)
+int oracle_query_norm(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy, uint64_t n,
+                      const int32_t* q, const int32_t* delta, uint64_t m, int w, int curve, int norm,
+                      uint64_t* counts, const uint64_t* offsets, uint32_t* out_ids,
+                      uint64_t* scanned, int threads)
 {
     if (threads < 1) threads = 1;
     if ((uint64_t)threads > m) threads = (int)(m ? m : 1);
@@ -321,7 +338,7 @@ int oracle_query(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy
     for (int t = 0; t < threads; ++t) {
         query_job* j = &jobs[t];
         j->skeys = skeys; j->sids = sids; j->sxy = sxy; j->n = n;
-        j->q = q; j->delta = delta; j->w = w; j->curve = curve;
+        j->q = q; j->delta = delta; j->w = w; j->curve = curve; j->norm = norm;
         j->m0 = m * (uint64_t)t / (uint64_t)threads;
         j->m1 = m * (uint64_t)(t + 1) / (uint64_t)threads;
         j->counts = counts; j->offsets = offsets; j->out_ids = out_ids; j->scanned = scanned;
@@ -337,13 +354,23 @@ int oracle_query(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy
     return 0;
 }
 
+/* Alg. 1 with the disc of the problem statement. */
+int oracle_query(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxy, uint64_t n,
+                 const int32_t* q, const int32_t* delta, uint64_t m, int w, int curve,
+                 uint64_t* counts, const uint64_t* offsets, uint32_t* out_ids,
+                 uint64_t* scanned, int threads)
+{
+    return oracle_query_norm(skeys, sids, sxy, n, q, delta, m, w, curve, 0, counts, offsets, out_ids,
+                             scanned, threads);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Brute force over the unsorted input: the problem statement of Sec. 2 taken literally.  */
 /* ------------------------------------------------------------------------------------ */
 
 typedef struct {
     const int32_t* xy; uint64_t n; const int32_t* q; const int32_t* delta;
-    uint64_t m0, m1; int w; uint64_t* counts; const uint64_t* offsets; uint32_t* out_ids;
+    uint64_t m0, m1; int w, norm; uint64_t* counts; const uint64_t* offsets; uint32_t* out_ids;
 } brute_job;
 
 static void* brute_worker(void* arg)
@@ -353,11 +380,10 @@ static void* brute_worker(void* arg)
         int32_t qx = j->q[2 * i], qy = j->q[2 * i + 1], dl = j->delta[i];
         uint64_t k = 0;
         if (query_valid(qx, qy, dl, j->w)) {
-            int64_t d2 = (int64_t)dl * (int64_t)dl;
             for (uint64_t p = 0; p < j->n; ++p) {
                 int64_t dx = (int64_t)j->xy[2 * p] - qx;
                 int64_t dy = (int64_t)j->xy[2 * p + 1] - qy;
-                if (dx * dx + dy * dy <= d2) {
+                if (in_window(dx, dy, dl, j->norm)) {
                     if (j->out_ids) j->out_ids[j->offsets[i] + k] = (uint32_t)p;
                     ++k;
                 }
@@ -369,9 +395,9 @@ static void* brute_worker(void* arg)
 }
 
 /* Per-query hits in ascending input index (not key) order. */
-int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t* delta,
-                 uint64_t m, int w, uint64_t* counts, const uint64_t* offsets,
-                 uint32_t* out_ids, int threads)
+int oracle_brute_norm(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t* delta,
+                      uint64_t m, int w, int norm, uint64_t* counts, const uint64_t* offsets,
+                      uint32_t* out_ids, int threads)
 {
     if (threads < 1) threads = 1;
     if ((uint64_t)threads > m) threads = (int)(m ? m : 1);
@@ -380,7 +406,7 @@ int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t*
     if (!jobs || !tids) { free(jobs); free(tids); return -2; }
     for (int t = 0; t < threads; ++t) {
         brute_job* j = &jobs[t];
-        j->xy = xy; j->n = n; j->q = q; j->delta = delta; j->w = w;
+        j->xy = xy; j->n = n; j->q = q; j->delta = delta; j->w = w; j->norm = norm;
         j->m0 = m * (uint64_t)t / (uint64_t)threads;
         j->m1 = m * (uint64_t)(t + 1) / (uint64_t)threads;
         j->counts = counts; j->offsets = offsets; j->out_ids = out_ids;
@@ -394,6 +420,13 @@ int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t*
     free(jobs);
     free(tids);
     return 0;
+}
+
+int oracle_brute(const int32_t* xy, uint64_t n, const int32_t* q, const int32_t* delta,
+                 uint64_t m, int w, uint64_t* counts, const uint64_t* offsets,
+                 uint32_t* out_ids, int threads)
+{
+    return oracle_brute_norm(xy, n, q, delta, m, w, 0, counts, offsets, out_ids, threads);
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -177,6 +177,24 @@ def normal_points(rng, n: int) -> np.ndarray:
     return _clamp_round(rng.normal(SIDE / 2, SIDE / 8, size=(n, 2)))
 
 
+def skewed_points(rng, n: int) -> np.ndarray:
+    """The paper's Skewed distribution (Sec. 3, "Data"): x uniform over the side, y geometric
+    with success probability 5 / side (mean side / 5), clamped to the domain."""
+    x = rng.integers(0, SIDE, size=n, dtype=np.int64)
+    y = np.minimum(rng.geometric(5.0 / SIDE, size=n) - 1, SIDE - 1)
+    return np.stack([x, y], axis=1).astype(np.int32)
+
+
+def paper_points(rng, dist: str, n: int) -> np.ndarray:
+    if dist == "uniform":
+        return uniform_points(rng, n)
+    if dist == "normal":
+        return normal_points(rng, n)
+    if dist == "skewed":
+        return skewed_points(rng, n)
+    raise ValueError(dist)
+
+
 def queries_at_points(rng, pts: np.ndarray, m: int):
     idx = rng.integers(0, pts.shape[0], size=m)
     return pts[idx].copy(), idx
@@ -285,6 +303,23 @@ def normal_uniform_queries(n: int, m: int, rel_side: float, seed: int = 6) -> Wo
     delta = max(0, int(round(rel_side * SIDE / 2)))
     return Workload("normal-uniform", pts, qs, np.full(m, delta, np.int32),
                     {"seed": seed, "rel_side": rel_side, "delta": delta})
+
+
+def paper_static(dist: str, n: int, m: int, rel_side: float, qdist: str = "uniform", seed: int = 7,
+                 scale: float = 1.0) -> Workload:
+    """The paper's static experiments (Sec. 3.1): points from its Uniform / Normal / Skewed
+    distributions, query centres from one of them, and square windows whose side is rel_side
+    times the domain side: the closed square of half-side delta = round(rel_side * side / 2)
+    (side 2 delta + 1 grid points), queried with norm "square"."""
+    n = max(2, int(round(n * scale)))
+    m = max(1, int(round(m * scale)))
+    rp, rq = _streams(seed, 2)
+    pts = paper_points(rp, dist, n)
+    qs = paper_points(rq, qdist, m)
+    delta = int(round(rel_side * SIDE / 2))
+    return Workload(f"paper-{dist}", pts, qs, np.full(m, delta, np.int32),
+                    {"seed": seed, "dist": dist, "qdist": qdist, "rel_side": rel_side, "delta": delta,
+                     "norm": "square"})
 
 
 WORKLOADS = {
