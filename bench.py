@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
-    ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5", "normal-1e7"],
+    ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5", "normal-1e7",
+                                           "paper-uniform", "paper-normal", "paper-skewed"],
                     default="mixed-1e7",
                     help="the headline is mixed-1e7; the others are supplementary measurements")
     ap.add_argument("--reorder", type=int, choices=[0, 1, 2], default=None,
@@ -54,7 +55,9 @@ def parse():
     ap.add_argument("--occupancy", type=int, default=0,
                     help="early-termination quadtree depth (0 = off; the paper uses 12)")
     ap.add_argument("--rel-side", type=float, default=1e-3,
-                    help="normal-1e7: query disc diameter relative to the domain side")
+                    help="normal-1e7: disc diameter; paper-*: square window side; relative to the domain side")
+    ap.add_argument("--n", type=float, default=1e7, help="paper-*: points")
+    ap.add_argument("--m", type=float, default=1e6, help="paper-*: queries (uniformly placed)")
     ap.add_argument("--cover", type=int, choices=[-1, 0, 1, 2], default=-1,
                     help="cover of each query's ball: 0 cells(Q), 1/2 levels finer, -1 autotuned")
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
@@ -88,7 +91,11 @@ def peaks():
 # --------------------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples (every 50 ms, time-stamped).  Started
+    before the warm-up so that the tool's own start-up does not fall inside the timed region;
+    only the samples taken between begin() and end() are reported (the nearest ones when the
+    region is shorter than the sampling period)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -96,6 +103,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
@@ -103,14 +111,33 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 5.0   # wait for the first sample
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -120,17 +147,23 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    rows.append((self._stamp(parts[0]), parts[1:]))
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        t0, t1 = self.t0 or 0.0, self.t1 or float("inf")
+        inside = [r for t, r in rows if t is not None and t0 <= t <= t1]
+        if len(inside) < 2:   # region shorter than the period: the samples nearest to it
+            mid = 0.5 * (t0 + t1)
+            stamped = sorted((abs(t - mid), i) for i, (t, r) in enumerate(rows) if t is not None)
+            inside = [rows[i][1] for _, i in stamped[:2]] or [r for _, r in rows]
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(inside)}
 
 
 # --------------------------------------------------------------------------------------
@@ -165,62 +198,56 @@ def run_ours(args, rank, world, local):
         opts["leaves"] = args.leaves
     if args.occupancy:
         opts["occupancy_depth"] = args.occupancy
+    norm = wl.meta.get("norm", "disc")
+    opts["query_norm"] = norm
 
     # size the output once (the total is the same for every step) and let the autotuner pick
-    # the scan's chunk size and work-queue batches for this shape (cached for later builds)
-    idx = sfc.sfc_build(pts, "z", **opts)
-    tuned = sfc.sfc_autotune(idx, q, d)
-    off, ids = sfc.query(idx, q, d)
+    # the cover, the scan's chunk size and work-queue batches for this shape
+    ix = sfc.sfc_build(pts, "z", **opts)
+    tuned = sfc.sfc_autotune(ix, q, d)
+    off, ids = sfc.query(ix, q, d)
     total = int(off[-1].item())
-    idx.close()
     ids = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
     off = torch.empty(m + 1, dtype=torch.int64, device=dev)
 
-    last = {}
-
     def step():
-        ix = sfc.sfc_build(pts, "z", **opts)
-        sfc.sfc_autotune(ix, q, d)          # applies the cached choice (no measurement)
+        # the whole build on the same index object (its buffers are reused, so steps allocate
+        # nothing): keys, sort, decode (+ model fit), then the query batch
+        sfc.sfc_rebuild(ix, pts)
         sfc.sfc_query_batch(ix, q, d, off, ids, capacity=total)
-        last["idx"] = ix
-        return ix
-
-    for _ in range(args.warmup):
-        step().close()
-    torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    sfc.sfc_profile_read(ix, reset=True)      # drop the warm-up records
+    clocks.begin()
     launches0 = sfc.sfc_launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    profs = []
     for i in range(args.steps):
         flush.fill_(i & 255)                      # evict L2 between timed steps
         ev[i][0].record()
-        ix = step()
+        step()
         ev[i][1].record()
-        profs.append(ix)
     torch.cuda.synchronize()
+    clocks.end()
     launches = sfc.sfc_launch_count() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     local_ms = sum(step_ms)
     total_ms = max_over_ranks(local_ms, pg, dev)
     # per-step device times of the library's steps (events on the launching stream)
-    agg = {}
-    for ix in profs:
-        for name, (cnt, ms) in sfc.sfc_profile_read(ix, reset=True).items():
-            c0, m0 = agg.get(name, (0, 0.0))
-            agg[name] = (c0 + cnt, m0 + ms)
-    stats = sfc.sfc_query_stats(profs[-1])
-    cell_stats = sfc.sfc_query_cell_stats(profs[-1])
-    status, bits = sfc.sfc_device_status(profs[-1])
-    for ix in profs:
-        ix.close()
+    agg = sfc.sfc_profile_read(ix, reset=True)
+    stats = sfc.sfc_query_stats(ix)
+    cell_stats = sfc.sfc_query_cell_stats(ix)
+    status, bits = sfc.sfc_device_status(ix)
+    ix.close()
     if status != 0:
         raise RuntimeError(f"device status {status} bits {bits:#x}")
 
@@ -237,10 +264,12 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "m": m, "curve": "z", "bounds": bounds,
+        "config": {"workload": args.workload, "n": n, "m": m, "curve": "z", "bounds": bounds, "window": norm,
+                   **({"rel_side": args.rel_side} if args.workload.startswith("paper-") or
+                      args.workload == "normal-1e7" else {}),
                    "reorder_queries": opts.get("reorder_queries", 2), "autotuned": tuned,
                    "seed": instance_seed(rank), "l2": "flushed between timed steps (256 MB write)",
-                   "step": "build (keys+sort+decode) + learned-model fit if enabled + query batch"},
+                   "step": "rebuild of the index (keys+sort+decode) + learned-model fit if enabled + query batch"},
         "roofline": {"kernel": "count_kernel", "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -259,7 +288,7 @@ def run_ours(args, rank, world, local):
         },
     }
     if rank == 0 and not args.no_extras:
-        bopts = {"cover_refine": tuned["cover"], "occupancy_depth": args.occupancy}
+        bopts = {"cover_refine": tuned["cover"], "occupancy_depth": args.occupancy, "query_norm": norm}
         if args.leaves is not None:
             bopts["leaves"] = args.leaves
         out["breakdown"].update(extras(sfc, torch, pts, q, d, total, n, m, flush, bopts))
@@ -298,6 +327,9 @@ def make_workload(args, rank):
         return workloads.mixed_1e8(scale=args.scale, seed=4 + 7919 * rank)
     if args.workload == "uniform-1e5":
         return workloads.uniform_1e5(scale=args.scale, seed=1 + 7919 * rank)
+    if args.workload.startswith("paper-"):
+        return workloads.paper_static(args.workload[6:], int(args.n), int(args.m), args.rel_side,
+                                      seed=7 + 7919 * rank, scale=args.scale)
     if args.workload == "normal-1e7":
         return workloads.normal_uniform_queries(max(2, int(10_000_000 * args.scale)),
                                                 max(1, int(1_000_000 * args.scale)), args.rel_side,
@@ -435,7 +467,7 @@ def e2e(sfc, torch, wl, total, bounds, args, cover):
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = sfc.sfc_build_host(hp, "z", bounds=bounds, cover_refine=cover)
+        ix = sfc.sfc_build_host(hp, "z", bounds=bounds, cover_refine=cover, query_norm=wl.meta.get("norm", "disc"))
         sfc.sfc_query_batch_host(ix, hq, hd, total, out_offsets=hoff, out_ids=hids)
         ix.close()
         torch.cuda.synchronize()
@@ -457,6 +489,7 @@ def oracle_sample(wl, budget_s: float, threads: int):
 
     t0 = time.perf_counter()
     idx = oracle.build(wl.points, 30, "z")
+    norm = wl.meta.get("norm", "disc")
     tb = time.perf_counter() - t0
     left = max(budget_s - tb, 1.0)
     k = 2000
@@ -467,7 +500,7 @@ def oracle_sample(wl, budget_s: float, threads: int):
         if k <= 0:
             break
         t1 = time.perf_counter()
-        oracle.query(idx, wl.queries[done:done + k], wl.delta[done:done + k], threads=threads)
+        oracle.query(idx, wl.queries[done:done + k], wl.delta[done:done + k], threads=threads, norm=norm)
         tq += time.perf_counter() - t1
         done += k
         if tq > left:
@@ -506,6 +539,7 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
            "data": "synthetic", "config": {"workload": args.workload, "n": wl.n, "m": wl.m, "curve": "z",
+                                           "window": wl.meta.get("norm", "disc"),
                                            "bounds": "binary (std lower_bound)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": (f"per step: oracle build of all {wl.n} points + the first "

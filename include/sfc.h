@@ -54,6 +54,11 @@ typedef enum { SFC_BOUNDS_BINARY = 0, SFC_BOUNDS_LEARNED = 1 } sfc_bounds;
 /* Root of the learned CDF model: monotone piecewise linear over 256 equal key intervals
  * (the key ranges of the level-4 quadtree cells), or a 1-16-1 monotone sigmoid MLP. */
 typedef enum { SFC_ROOT_PWL = 0, SFC_ROOT_MLP = 1 } sfc_root;
+/* Query window.  SFC_NORM_DISC: the closed disc (x - q_x)^2 + (y - q_y)^2 <= delta^2 of the
+ * problem statement (Sec. 2).  SFC_NORM_SQUARE: the closed axis-parallel square
+ * max(|x - q_x|, |y - q_y|) <= delta (side 2 delta + 1 grid points), the square windows of the
+ * paper's experiments (Sec. 3, "Queries"). */
+typedef enum { SFC_NORM_DISC = 0, SFC_NORM_SQUARE = 1 } sfc_norm;
 
 /* Device status bits (sfc_device_status_bits). */
 #define SFC_DEV_BAD_POINT   0x1u   /* a point coordinate outside [0, 2^30) */
@@ -91,6 +96,7 @@ typedef struct {
                                cells of their cover that it shows empty (a cell deeper than D
                                answers for its depth-D ancestor).  0 = off, 1..13; D = 12 (the
                                paper's) takes 2.8 MB (default 0) */
+    sfc_norm query_norm;    /* window of the queries (default SFC_NORM_DISC); sfc_set_query_norm */
 } sfc_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -226,6 +232,11 @@ sfc_status sfc_get_occupancy(const sfc_index* idx, uint32_t* d_out, uint64_t wor
 /* Cover statistics of the last query batch: *h_cells the cells of all covers, *h_empty those
  * dropped as empty by the early-termination bitmap.  Synchronises `stream`. */
 sfc_status sfc_query_cell_stats(const sfc_index* idx, uint64_t* h_cells, uint64_t* h_empty, void* stream);
+
+/* Sets the window of later queries (SFC_NORM_DISC or SFC_NORM_SQUARE, else SFC_ERR_INVALID).
+ * A count already made keeps its window for its write; a captured query graph keeps the window
+ * it was captured with. */
+sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm);
 
 /* The cover currently used by queries (0, 1 or 2), or -1 for idx == NULL. */
 int sfc_cover_refine(const sfc_index* idx);

@@ -49,7 +49,8 @@ class sfc_options(ctypes.Structure):
                 ("train_samples", ctypes.c_int), ("learning_rate", ctypes.c_float),
                 ("chunk", ctypes.c_int), ("mask_budget_mb", ctypes.c_int),
                 ("reorder_queries", ctypes.c_int), ("profile", ctypes.c_int), ("root", ctypes.c_int),
-                ("cover_refine", ctypes.c_int), ("occupancy_depth", ctypes.c_int)]
+                ("cover_refine", ctypes.c_int), ("occupancy_depth", ctypes.c_int),
+                ("query_norm", ctypes.c_int)]
 
 
 class sfc_profile_entry(ctypes.Structure):
@@ -87,6 +88,7 @@ def lib():
             "sfc_reserve_queries": (ci, [P, u64, P]),
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_set_cover": (ci, [P, ci]),
+            "sfc_set_query_norm": (ci, [P, ci]),
             "sfc_get_occupancy": (ci, [P, P, u64, P, P]),
             "sfc_query_cell_stats": (ci, [P, P, P, P]),
             "sfc_cover_refine": (ci, [P]),
@@ -205,6 +207,8 @@ def sfc_default_options(**overrides) -> sfc_options:
             v = _bounds(v)
         if k == "root":
             v = _root(v)
+        if k == "query_norm":
+            v = _norm(v)
         setattr(o, k, v)
     return o
 
@@ -406,6 +410,22 @@ def sfc_query_cell_stats(index: Index, stream=None) -> dict:
     _check(lib().sfc_query_cell_stats(index.handle, ctypes.byref(c), ctypes.byref(e), _stream(stream)),
            "sfc_query_cell_stats")
     return {"cells": c.value, "empty": e.value}
+
+
+SFC_NORM_DISC = 0
+SFC_NORM_SQUARE = 1
+
+
+def _norm(norm) -> int:
+    if norm in (SFC_NORM_DISC, "disc", "l2"):
+        return SFC_NORM_DISC
+    if norm in (SFC_NORM_SQUARE, "square", "box", "linf"):
+        return SFC_NORM_SQUARE
+    raise ValueError(f"unknown query norm {norm!r}")
+
+
+def sfc_set_query_norm(index: Index, norm):
+    _check(lib().sfc_set_query_norm(index.handle, _norm(norm)), "sfc_set_query_norm")
 
 
 def sfc_set_cover(index: Index, refine: int):

@@ -137,6 +137,7 @@ QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint
     a.status = status_word(idx);
     a.drop = idx->drop;
     a.kint = (uint32_t)cover_intervals(idx->drop);
+    a.norm = idx->norm;
     if (idx->opt.occupancy_depth > 0 && idx->occ.ptr) {
         a.occ = idx->occ.as<uint32_t>();
         a.occ_depth = idx->opt.occupancy_depth;
@@ -194,7 +195,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     SFC_TRY(ensure_status_buf(idx, st));
     if (m == 0) {
         SFC_CUDA_TRY(cudaMemsetAsync(d_out_offsets, 0, sizeof(uint64_t), st));
-        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0, false, idx->drop};
+        idx->qws.pending = {true, d_q, d_delta, 0, d_out_offsets, 0, false, idx->drop, idx->norm};
         return SFC_OK;
     }
     SFC_TRY(ensure_query_ws(idx, m, st));
@@ -254,7 +255,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         ProfScope ps(idx, "scan", st);
         SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
     }
-    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered, a.drop};
+    w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered, a.drop, a.norm};
     return SFC_OK;
 }
 
@@ -270,6 +271,7 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     QueryArgs a = base_args(idx, d_q, d_delta, m);
     a.drop = w.pending.drop;
     a.kint = (uint32_t)cover_intervals(a.drop);
+    a.norm = w.pending.norm;
     a.ranges = w.ranges.as<uint32_t>();
     a.nchunks = w.nchunks.as<uint32_t>();
     a.chunk_base = w.chunk_base.as<uint64_t>();
@@ -312,6 +314,7 @@ void sfc_default_options(sfc_options* opt)
     opt->root = SFC_ROOT_PWL;
     opt->cover_refine = 0;
     opt->occupancy_depth = 0;
+    opt->query_norm = SFC_NORM_DISC;
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
@@ -328,7 +331,8 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
         o.train_steps < 0 || o.reorder_queries < 0 || o.reorder_queries > 2 || (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))) ||
         (o.bounds != SFC_BOUNDS_BINARY && o.bounds != SFC_BOUNDS_LEARNED) ||
         (o.root != SFC_ROOT_PWL && o.root != SFC_ROOT_MLP) || o.cover_refine < -1 || o.cover_refine > 2 ||
-        o.occupancy_depth < 0 || o.occupancy_depth > 13)
+        o.occupancy_depth < 0 || o.occupancy_depth > 13 ||
+        (o.query_norm != SFC_NORM_DISC && o.query_norm != SFC_NORM_SQUARE))
         return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     sfc_index* idx = new (std::nothrow) sfc_index();
@@ -340,6 +344,7 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     idx->bounds = SFC_BOUNDS_BINARY;
     idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;
     idx->drop = o.cover_refine < 0 ? 1 : o.cover_refine;
+    idx->norm = o.query_norm;
     idx->last_stream = st;
     idx->prof.on = o.profile != 0;
     sfc_status s = ensure_status_buf(idx, st);
@@ -514,11 +519,11 @@ sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_
 namespace {
 
 struct TuneKey {
-    int device, curve, lgn, lgm, bounds, cover;   // cover: the option (-1 = tuned)
+    int device, curve, lgn, lgm, bounds, cover, norm;   // cover: the option (-1 = tuned)
     bool operator==(const TuneKey& o) const
     {
         return device == o.device && curve == o.curve && lgn == o.lgn && lgm == o.lgm && bounds == o.bounds &&
-               cover == o.cover;
+               cover == o.cover && norm == o.norm;
     }
 };
 
@@ -571,7 +576,7 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
     if (!idx || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     const TuneKey key{idx->device, (int)idx->curve, lg2(idx->n + 1), lg2(m + 1), (int)idx->bounds,
-                      idx->opt.cover_refine};
+                      idx->opt.cover_refine, idx->norm};
     bool cached = false;
     if (!force) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -660,6 +665,13 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
     if (h_chunk) *h_chunk = (int)idx->chunk;
     if (h_batch) *h_batch = (int)idx->batch;
     if (h_qbatch) *h_qbatch = (int)idx->qbatch;
+    return SFC_OK;
+}
+
+sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm)
+{
+    if (!idx || (norm != SFC_NORM_DISC && norm != SFC_NORM_SQUARE)) return SFC_ERR_INVALID;
+    idx->norm = norm;
     return SFC_OK;
 }
 

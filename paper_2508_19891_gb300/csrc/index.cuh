@@ -16,12 +16,13 @@ struct PendingCount {       // plan kept between sfc_query_count and sfc_query_w
     uint32_t chunk;
     bool ordered;           // queries processed in curve order (perm / wbase valid)
     int drop;               // cover refinement of the plan
+    int norm;               // query window of the plan
 };
 
 struct QueryWs {
     DevBuf ranges, nchunks, chunk_base, counts, masks, ctr;
     DevBuf qkeys, qkeys_sorted, perm, nch_sorted, wbase;   // curve-order processing
-    PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false, 0};
+    PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false, 0, 0};
 };
 
 struct HostStage {          // device staging of sfc_query_batch_host
@@ -69,6 +70,7 @@ struct sfc_index {
     uint32_t batch = 4;                 // chunks per work-queue grab
     uint32_t qbatch = 8;                // queries per write-queue grab
     int drop = 0;                       // cover refinement: levels below cells(Q) (0..2)
+    int norm = 0;                       // query window (sfc_norm)
     cudaStream_t last_stream = nullptr;
 
     sfc::DevBuf keys, ids, xy;          // the sorted array A_P and its keys

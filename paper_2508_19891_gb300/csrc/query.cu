@@ -180,11 +180,12 @@ __device__ __forceinline__ bool cell_occupied(const uint32_t* __restrict__ occ, 
 // DROP 0: cells(Q), the cells of level l (2 delta <= 2^l < 4 delta, capped at omega) that meet
 // the clipped square Q.  DROP > 0: the cells of level max(0, l - DROP) that hold an integer
 // point of the closed ball (the distance from q to the cell's nearest integer point is at most
-// delta).  Each cell gives the key interval [pi(C)o0, pi(C)o1] (Observation).  With the
+// delta; for the square window every cell meeting Q qualifies).  Each cell gives the key
+// interval [pi(C)o0, pi(C)o1] (Observation).  With the
 // early-termination bitmap (occ != NULL), cells it shows empty are dropped; ncell / nempty
 // count the cover's cells and the dropped ones.
 template <int DROP>
-__device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb, int32_t qx, int32_t qy,
+__device__ __forceinline__ int derive_ranges(int curve, int norm, const HilbertTables* tb, int32_t qx, int32_t qy,
                                              int32_t delta, const uint32_t* occ, int D, uint64_t* lo,
                                              uint64_t* hi, uint32_t& ncell, uint32_t& nempty)
 {
@@ -202,7 +203,7 @@ __device__ __forceinline__ int derive_ranges(int curve, const HilbertTables* tb,
     int cnt = 0;
     for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
         for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
-            if (DROP > 0) {
+            if (DROP > 0 && norm == SFC_NORM_DISC) {   // every cell meeting Q meets a square window
                 const int64_t ax0 = cx << l, ax1 = ((cx + 1) << l) - 1;
                 const int64_t ay0 = cy << l, ay1 = ((cy + 1) << l) - 1;
                 const int64_t dx = qx < ax0 ? ax0 - qx : (qx > ax1 ? qx - ax1 : 0);
@@ -250,7 +251,8 @@ __device__ __forceinline__ int query_bounds(const Bounds& bounds, const QueryArg
     constexpr int NB = (2 * K + 7) / 8;
     const uint64_t* keys = a.keys;
     const uint32_t n = a.n;
-    const int cnt = derive_ranges<DROP>(a.curve, tb, qx, qy, delta, a.occ, a.occ_depth, lo, hi, ncell, nempty);
+    const int cnt = derive_ranges<DROP>(a.curve, a.norm, tb, qx, qy, delta, a.occ, a.occ_depth, lo, hi, ncell,
+                                        nempty);
     const int ne = 2 * cnt;
 #pragma unroll 1
     for (int bi = 0; bi < NB && 8 * bi < ne; ++bi) {
@@ -373,7 +375,8 @@ struct QView {
     uint32_t S;      // concatenated length (sum of the interval lengths)
     uint32_t nint;   // intervals stored per query
     int2 q;
-    int64_t d2;
+    int32_t d;       // delta
+    int64_t d2;      // delta^2
 };
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
@@ -408,8 +411,8 @@ __device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi, War
     v.S = __shfl_sync(0xffffffffu, incl, 31);
     v.nint = a.kint;
     v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
-    const int64_t d = __ldg(a.delta + qi);
-    v.d2 = d * d;
+    v.d = __ldg(a.delta + qi);
+    v.d2 = (int64_t)v.d * v.d;
     return v;
 }
 
@@ -422,11 +425,14 @@ __device__ __forceinline__ void seek(const WarpTab* tab, uint32_t nint, uint32_t
     end = tab->end[r];
 }
 
-// Exact closed-ball test: |dx|, |dy| < 2^30, so each square is one signed 32x32 -> 64-bit
-// multiply(-add) and the sum stays below 2^61.
+// Exact window tests.  Disc (the problem statement's closed ball): |dx|, |dy| < 2^30, so each
+// square is one signed 32x32 -> 64-bit multiply(-add) and the sum stays below 2^61.  Square
+// (the experiments' windows): max(|dx|, |dy|) <= delta in 32-bit integers.
+template <int NORM>
 __device__ __forceinline__ bool is_hit(const QView& v, int2 p)
 {
     const int dx = p.x - v.q.x, dy = p.y - v.q.y;
+    if (NORM == SFC_NORM_SQUARE) return max(abs(dx), abs(dy)) <= v.d;
     const long long s = (long long)dx * dx + (long long)dy * dy;
     return s <= v.d2;
 }
@@ -452,7 +458,7 @@ __device__ __forceinline__ void keep_words(uint32_t (&words)[WPL], uint32_t it, 
 // groups of 4 x 32: when the whole group lies inside the chunk and no lane crosses the end of
 // its interval (one vote), the group runs without per-point guards; otherwise each point is
 // checked and the lane looks its interval up again when it crosses into the next one.
-template <int WPL>
+template <int WPL, int NORM>
 __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, const WarpTab* tab,
                                                  uint32_t s0, uint32_t s1, uint32_t (&words)[WPL])
 {
@@ -468,10 +474,10 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
         if (full && __all_sync(0xffffffffu, f + 96 < end)) {
             const int2* p = xy + (f + shift);
             const int2 p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
-            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit(v, p0));
-            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit(v, p1));
-            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit(v, p2));
-            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit(v, p3));
+            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p0));
+            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p1));
+            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p2));
+            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p3));
             keep_words<WPL>(words, it, w0, w1, w2, w3);
         } else {
             int2 p[4];
@@ -485,7 +491,7 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
             }
             uint32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit(v, p[u]));
+            for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit<NORM>(v, p[u]));
             keep_words<WPL>(words, it, w[0], w[1], w[2], w[3]);
         }
     }
@@ -519,7 +525,7 @@ __device__ __forceinline__ uint64_t owner_query(const uint64_t* __restrict__ bas
 // ------------------------------------------------------------------------------------
 // count_kernel
 // ------------------------------------------------------------------------------------
-template <int WPL>
+template <int WPL, int NORM>
 __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 {
     __shared__ WarpTab s_tab[kThreads / 32];
@@ -550,7 +556,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
             const uint32_t s0 = j * a.chunk;
             const uint32_t s1 = min(v.S, s0 + a.chunk);
             uint32_t words[WPL];
-            const uint32_t cnt = filter_chunk<WPL>(a, v, tab, s0, s1, words);
+            const uint32_t cnt = filter_chunk<WPL, NORM>(a, v, tab, s0, s1, words);
             if (g < a.mask_chunks) {
                 const uint32_t nw = (s1 - s0 + 31) >> 5;
                 uint32_t* mp = a.masks + g * W;
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 // ------------------------------------------------------------------------------------
 // write_kernel
 // ------------------------------------------------------------------------------------
-template <int WPL>
+template <int WPL, int NORM>
 __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
 {
     // per-warp staging of the array positions of one group of 32 mask words (<= 1024 hits)
@@ -610,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                         words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
                     }
                 } else {
-                    filter_chunk<WPL>(a, v, tab, s0, s1, words);
+                    filter_chunk<WPL, NORM>(a, v, tab, s0, s1, words);
                 }
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
@@ -677,16 +683,23 @@ int persistent_grid(const void* fn)
     return per_sm * num_sms();
 }
 
+template <int WPL, int NORM>
+void launch_count_write_norm(const QueryArgs& a, bool write, cudaStream_t st)
+{
+    if (!write) {
+        int g = persistent_grid((const void*)count_kernel<WPL, NORM>);
+        count_kernel<WPL, NORM><<<g, kThreads, 0, st>>>(a);
+    } else {
+        int g = persistent_grid((const void*)write_kernel<WPL, NORM>);
+        write_kernel<WPL, NORM><<<g, kThreads, 0, st>>>(a);
+    }
+}
+
 template <int WPL>
 sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 {
-    if (!write) {
-        int g = persistent_grid((const void*)count_kernel<WPL>);
-        count_kernel<WPL><<<g, kThreads, 0, st>>>(a);
-    } else {
-        int g = persistent_grid((const void*)write_kernel<WPL>);
-        write_kernel<WPL><<<g, kThreads, 0, st>>>(a);
-    }
+    if (a.norm == SFC_NORM_SQUARE) launch_count_write_norm<WPL, SFC_NORM_SQUARE>(a, write, st);
+    else launch_count_write_norm<WPL, SFC_NORM_DISC>(a, write, st);
     count_launch();
     return launch_status();
 }

@@ -17,6 +17,7 @@ struct QueryArgs {
     uint32_t* ranges;            // [m][2 * kint]: (begin, end) of up to kint intervals
     uint32_t kint;               // intervals stored per query (4, 9 or 25 by the cover)
     int drop;                    // cover refinement: 0 cells(Q), 1 or 2 levels finer
+    int norm;                    // SFC_NORM_DISC or SFC_NORM_SQUARE
     uint32_t* nchunks;           // [m]
     uint64_t* chunk_base;        // [m + 1]
     uint32_t* counts;            // [m] hits per query
