@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the 
 reference leg of ``bench.py`` may import this package.  It shares no code with the CUDA
 library and the CUDA library never calls it.
 
-The heavy parts (keys, the sort, Alg. 1, brute force) are plain C in ``oracle.c``, compiled
+The heavy parts (keys, the sort, Alg. 1, brute force, the early-termination quadtree, the 3-D
+Z curve) are plain C in ``oracle.c``, compiled
 here with gcc into ``liboracle.so`` and called through ctypes; this module only marshals
 numpy arrays.  ``learned.py`` holds the fp64 reference of the learned-bounds model and
 ``dynamic.py`` the rebuild-from-scratch oracle of the dynamic setting.
@@ -31,6 +32,7 @@ _lib = None
 CURVE_Z = 0
 CURVE_HILBERT = 1
 OMEGA = 30  # bits per coordinate on the GPU path
+OMEGA3 = 21  # bits per coordinate of 3-D points on the GPU path (63-bit keys)
 
 
 NORM_DISC = 0     # closed disc dx^2 + dy^2 <= delta^2 (problem statement)
@@ -98,6 +100,16 @@ def _L():
         lib.oracle_brute_norm.argtypes = [P, u64, P, P, u64, c_int, c_int, P, P, P, c_int]
         lib.oracle_cells_refined_norm.restype = c_int
         lib.oracle_cells_refined_norm.argtypes = [i32, i32, i32, c_int, c_int, c_int, c_int, P, P, c_int]
+        lib.oracle_key_z3.restype = u64
+        lib.oracle_key_z3.argtypes = [u32, u32, u32, c_int]
+        lib.oracle_build3.restype = c_int
+        lib.oracle_build3.argtypes = [P, u64, c_int, P, P, P]
+        lib.oracle_cells3.restype = c_int
+        lib.oracle_cells3.argtypes = [i32, i32, i32, i32, c_int, P, P, P]
+        lib.oracle_query3.restype = c_int
+        lib.oracle_query3.argtypes = [P, P, P, u64, P, P, u64, c_int, P, P, P]
+        lib.oracle_brute3.restype = c_int
+        lib.oracle_brute3.argtypes = [P, u64, P, P, u64, c_int, P, P, P]
         lib.oracle_query.restype = c_int
         lib.oracle_query.argtypes = [P, P, P, u64, P, P, u64, c_int, c_int, P, P, P, P, c_int]
         lib.oracle_brute.restype = c_int
@@ -279,3 +291,70 @@ def sorted_lists(offsets: np.ndarray, ids: np.ndarray):
     """Per-query id lists, each sorted ascending (the unique part of a result)."""
     offsets = np.asarray(offsets, dtype=np.int64)
     return [np.sort(ids[offsets[i]:offsets[i + 1]]) for i in range(offsets.shape[0] - 1)]
+
+
+# --------------------------------------------------------------------------------------
+# d = 3 (the Z curve in Z^3)
+# --------------------------------------------------------------------------------------
+
+def key_z3(x: int, y: int, z: int, w: int = OMEGA3) -> int:
+    return int(_L().oracle_key_z3(int(x), int(y), int(z), int(w)))
+
+
+def keys3(xyz: np.ndarray, w: int = OMEGA3) -> np.ndarray:
+    xyz = _c(xyz, np.int64).reshape(-1, 3)
+    return np.array([key_z3(a, b, c, w) for a, b, c in xyz], dtype=np.uint64)
+
+
+def build3(xyz: np.ndarray, w: int = OMEGA3) -> Index:
+    xyz = _c(xyz, np.int32).reshape(-1, 3)
+    n = xyz.shape[0]
+    sk = np.empty(n, np.uint64)
+    si = np.empty(n, np.uint32)
+    sxyz = np.empty((n, 3), np.int32)
+    if _L().oracle_build3(_ptr(xyz), n, int(w), _ptr(sk), _ptr(si), _ptr(sxyz)) != 0:
+        raise MemoryError("oracle_build3 failed")
+    return Index(sk, si, sxyz, int(w), CURVE_Z)
+
+
+def cells3(qx: int, qy: int, qz: int, delta: int, w: int = OMEGA3):
+    """Key intervals [lo, hi] of cells(Q) in 3-D, sorted by lo, and the level l."""
+    lo = np.zeros(8, np.uint64)
+    hi = np.zeros(8, np.uint64)
+    lv = ctypes.c_int(0)
+    cnt = _L().oracle_cells3(int(qx), int(qy), int(qz), int(delta), int(w), _ptr(lo), _ptr(hi), ctypes.byref(lv))
+    if cnt < 0:
+        raise AssertionError("more than eight cells")
+    return [(int(lo[i]), int(hi[i])) for i in range(cnt)], int(lv.value)
+
+
+def query3(index: Index, q: np.ndarray, delta: np.ndarray):
+    """Alg. 1 in 3-D (closed ball); offsets u64[m+1], ids in ascending (key, id) order."""
+    q = _c(q, np.int32).reshape(-1, 3)
+    delta = _c(delta, np.int32).reshape(-1)
+    m = q.shape[0]
+    counts = np.empty(m, np.uint64)
+    L = _L()
+    L.oracle_query3(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q), _ptr(delta), m,
+                    index.w, _ptr(counts), None, None)
+    offsets = np.zeros(m + 1, np.uint64)
+    np.cumsum(counts, out=offsets[1:])
+    ids = np.empty(int(offsets[m]), np.uint32)
+    L.oracle_query3(_ptr(index.keys), _ptr(index.ids), _ptr(index.xy), index.n, _ptr(q), _ptr(delta), m,
+                    index.w, None, _ptr(offsets), _ptr(ids))
+    return offsets, ids
+
+
+def brute3(xyz: np.ndarray, q: np.ndarray, delta: np.ndarray, w: int = OMEGA3):
+    xyz = _c(xyz, np.int32).reshape(-1, 3)
+    q = _c(q, np.int32).reshape(-1, 3)
+    delta = _c(delta, np.int32).reshape(-1)
+    m = q.shape[0]
+    counts = np.empty(m, np.uint64)
+    L = _L()
+    L.oracle_brute3(_ptr(xyz), xyz.shape[0], _ptr(q), _ptr(delta), m, int(w), _ptr(counts), None, None)
+    offsets = np.zeros(m + 1, np.uint64)
+    np.cumsum(counts, out=offsets[1:])
+    ids = np.empty(int(offsets[m]), np.uint32)
+    L.oracle_brute3(_ptr(xyz), xyz.shape[0], _ptr(q), _ptr(delta), m, int(w), None, _ptr(offsets), _ptr(ids))
+    return offsets, ids

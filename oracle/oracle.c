@@ -464,3 +464,143 @@ int oracle_cell_occupied(const uint32_t* bits, int w, int D, int l, uint64_t lo)
     const uint64_t b = start + (lo >> (2 * (w - t)));
     return (int)((bits[b / 32] >> (b % 32)) & 1u);
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* d = 3: the Z curve in Z^3 (the paper notes its Z implementation extends to R^d,       */
+/* Sec. 2.1; cells(Q) then has at most 2^d = 8 cells, Sec. 1.2).                         */
+/* Domain [0, 2^w)^3; pi(p) has 3w bits: bit 3i = x_i, bit 3i+1 = y_i, bit 3i+2 = z_i     */
+/* (Alg. 2 with a third interleaved coordinate).  The GPU path fixes w = 21 (63 bits).   */
+/* ------------------------------------------------------------------------------------ */
+
+/* Z key in 3-D, the literal per-bit loop. */
+uint64_t oracle_key_z3(uint32_t x, uint32_t y, uint32_t z, int w)
+{
+    uint64_t out = 0;
+    for (int i = 0; i < w; ++i) {
+        out |= (uint64_t)((x >> i) & 1u) << (3 * i);
+        out |= (uint64_t)((y >> i) & 1u) << (3 * i + 1);
+        out |= (uint64_t)((z >> i) & 1u) << (3 * i + 2);
+    }
+    return out;
+}
+
+/* Sorted array of 3-D points: keys, input indices and coordinates sorted by (key, id). */
+int oracle_build3(const int32_t* xyz, uint64_t n, int w, uint64_t* skeys, uint32_t* sids, int32_t* sxyz)
+{
+    oracle_pair* pairs = (oracle_pair*)malloc((n ? n : 1) * sizeof(oracle_pair));
+    if (!pairs) return -2;
+    for (uint64_t i = 0; i < n; ++i) {
+        pairs[i].key = oracle_key_z3((uint32_t)xyz[3 * i], (uint32_t)xyz[3 * i + 1], (uint32_t)xyz[3 * i + 2], w);
+        pairs[i].id = (uint32_t)i;
+    }
+    qsort(pairs, n, sizeof(oracle_pair), pair_cmp);
+    for (uint64_t i = 0; i < n; ++i) {
+        skeys[i] = pairs[i].key;
+        sids[i] = pairs[i].id;
+        for (int c = 0; c < 3; ++c) sxyz[3 * i + c] = xyz[3 * (uint64_t)pairs[i].id + c];
+    }
+    free(pairs);
+    return 0;
+}
+
+/* cells(Q) in 3-D: Q = [q - delta, q + delta]^3 clipped to the domain, level l as in 2-D
+ * (side 2^l with 2 delta <= 2^l < 4 delta, capped at w), the cells of that level meeting Q
+ * (at most two per axis, so at most 8), each with the key interval [pi(C)o0, pi(C)o1] of
+ * length 8^l; sorted by lo. */
+int oracle_cells3(int32_t qx, int32_t qy, int32_t qz, int32_t delta, int w, uint64_t lo[8], uint64_t hi[8],
+                  int* level_out)
+{
+    const int64_t side = (int64_t)1 << w;
+    const int64_t d = delta;
+    int64_t a0[3], a1[3];
+    const int64_t c[3] = {qx, qy, qz};
+    for (int k = 0; k < 3; ++k) {
+        a0[k] = c[k] - d < 0 ? 0 : c[k] - d;
+        a1[k] = c[k] + d > side - 1 ? side - 1 : c[k] + d;
+    }
+    const int l = oracle_level(d, w);
+    if (level_out) *level_out = l;
+    int cnt = 0;
+    for (int64_t cz = a0[2] >> l; cz <= (a1[2] >> l); ++cz)
+        for (int64_t cy = a0[1] >> l; cy <= (a1[1] >> l); ++cy)
+            for (int64_t cx = a0[0] >> l; cx <= (a1[0] >> l); ++cx) {
+                if (cnt == 8) return -1;   /* cannot happen: at most two cells per axis */
+                const uint64_t corner = oracle_key_z3((uint32_t)(cx << l), (uint32_t)(cy << l), (uint32_t)(cz << l), w);
+                const uint64_t span = (3 * l >= 64) ? ~(uint64_t)0 : (((uint64_t)1 << (3 * l)) - 1);
+                lo[cnt] = corner & ~span;
+                hi[cnt] = lo[cnt] + span;
+                ++cnt;
+            }
+    for (int i = 1; i < cnt; ++i) {
+        const uint64_t a = lo[i], b = hi[i];
+        int j = i - 1;
+        while (j >= 0 && lo[j] > a) { lo[j + 1] = lo[j]; hi[j + 1] = hi[j]; --j; }
+        lo[j + 1] = a; hi[j + 1] = b;
+    }
+    return cnt;
+}
+
+static int query3_valid(int32_t qx, int32_t qy, int32_t qz, int32_t delta, int w)
+{
+    const int64_t side = (int64_t)1 << w;
+    return qx >= 0 && qy >= 0 && qz >= 0 && qx < side && qy < side && qz < side && delta >= 0;
+}
+
+/* Alg. 1 in 3-D for queries [m0, m1): closed ball dx^2 + dy^2 + dz^2 <= delta^2 in int64. */
+static uint64_t query3_one(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxyz, uint64_t n,
+                           const int32_t* q, int32_t delta, int w, uint32_t* out)
+{
+    if (!query3_valid(q[0], q[1], q[2], delta, w)) return 0;
+    uint64_t lo[8], hi[8];
+    const int cnt = oracle_cells3(q[0], q[1], q[2], delta, w, lo, hi, NULL);
+    const int64_t d2 = (int64_t)delta * delta;
+    uint64_t k = 0;
+    for (int c = 0; c < cnt; ++c) {
+        for (uint64_t x = oracle_lower_bound(skeys, n, lo[c]); x < n && skeys[x] <= hi[c]; ++x) {
+            const int64_t dx = (int64_t)sxyz[3 * x] - q[0];
+            const int64_t dy = (int64_t)sxyz[3 * x + 1] - q[1];
+            const int64_t dz = (int64_t)sxyz[3 * x + 2] - q[2];
+            if (dx * dx + dy * dy + dz * dz <= d2) {
+                if (out) out[k] = sids[x];
+                ++k;
+            }
+        }
+    }
+    return k;
+}
+
+/* Counts (offsets == NULL) or ids (written at out_ids + offsets[i]) of every query, one thread. */
+int oracle_query3(const uint64_t* skeys, const uint32_t* sids, const int32_t* sxyz, uint64_t n,
+                  const int32_t* q, const int32_t* delta, uint64_t m, int w, uint64_t* counts,
+                  const uint64_t* offsets, uint32_t* out_ids)
+{
+    for (uint64_t i = 0; i < m; ++i) {
+        const uint64_t k = query3_one(skeys, sids, sxyz, n, q + 3 * i, delta[i], w,
+                                      out_ids ? out_ids + offsets[i] : NULL);
+        if (counts) counts[i] = k;
+    }
+    return 0;
+}
+
+/* Brute force in 3-D: ids ascending per query. */
+int oracle_brute3(const int32_t* xyz, uint64_t n, const int32_t* q, const int32_t* delta, uint64_t m, int w,
+                  uint64_t* counts, const uint64_t* offsets, uint32_t* out_ids)
+{
+    for (uint64_t i = 0; i < m; ++i) {
+        uint64_t k = 0;
+        if (query3_valid(q[3 * i], q[3 * i + 1], q[3 * i + 2], delta[i], w)) {
+            const int64_t d2 = (int64_t)delta[i] * delta[i];
+            for (uint64_t p = 0; p < n; ++p) {
+                const int64_t dx = (int64_t)xyz[3 * p] - q[3 * i];
+                const int64_t dy = (int64_t)xyz[3 * p + 1] - q[3 * i + 1];
+                const int64_t dz = (int64_t)xyz[3 * p + 2] - q[3 * i + 2];
+                if (dx * dx + dy * dy + dz * dz <= d2) {
+                    if (out_ids) out_ids[offsets[i] + k] = (uint32_t)p;
+                    ++k;
+                }
+            }
+        }
+        if (counts) counts[i] = k;
+    }
+    return 0;
+}
