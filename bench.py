@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--bounds", choices=["learned", "binary"], default=None)
     ap.add_argument("--workload", choices=["mixed-1e7", "mixed-1e8", "uniform-1e5", "normal-1e7",
-                                           "paper-uniform", "paper-normal", "paper-skewed"],
+                                           "paper-uniform", "paper-normal", "paper-skewed", "mixed3d-1e7"],
                     default="mixed-1e7",
                     help="the headline is mixed-1e7; the others are supplementary measurements")
     ap.add_argument("--reorder", type=int, choices=[0, 1, 2], default=None,
@@ -184,7 +184,11 @@ def run_ours(args, rank, world, local):
 
     wl = make_workload(args, rank)
     n, m = wl.n, wl.m
-    bounds = args.bounds or ("learned" if learned_available(sfc) else "binary")
+    dim = wl.meta.get("dim", 2)
+    if dim == 3:   # 3-D indexes search with binary bounds only
+        bounds = "binary"
+    else:
+        bounds = args.bounds or ("learned" if learned_available(sfc) else "binary")
     pts = torch.from_numpy(wl.points).to(dev)
     q = torch.from_numpy(wl.queries).to(dev)
     d = torch.from_numpy(wl.delta).to(dev)
@@ -200,10 +204,12 @@ def run_ours(args, rank, world, local):
         opts["occupancy_depth"] = args.occupancy
     norm = wl.meta.get("norm", "disc")
     opts["query_norm"] = norm
+    if dim == 3:
+        opts = {"profile": 1}
 
     # size the output once (the total is the same for every step) and let the autotuner pick
     # the cover, the scan's chunk size and work-queue batches for this shape
-    ix = sfc.sfc_build(pts, "z", **opts)
+    ix = sfc.sfc_build3(pts, **opts) if dim == 3 else sfc.sfc_build(pts, "z", **opts)
     tuned = sfc.sfc_autotune(ix, q, d)
     off, ids = sfc.query(ix, q, d)
     total = int(off[-1].item())
@@ -258,13 +264,15 @@ def run_ours(args, rank, world, local):
     count_runs, count_ms = agg.get("count", (0, float("nan")))
     count_avg_ms = count_ms / max(count_runs, 1)
     S = stats["scanned"]
-    alg_bytes = 8 * S + S // 8          # coordinates read + one mask bit per scanned point
+    # coordinates read (x, y[, z] as int32) + one mask bit per scanned point
+    alg_bytes = 4 * dim * S + S // 8
     achieved = alg_bytes / (count_avg_ms / 1e3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "m": m, "curve": "z", "bounds": bounds, "window": norm,
+        "config": {"workload": args.workload, "n": n, "m": m, "dim": dim, "curve": "z", "bounds": bounds,
+                   "window": norm,
                    **({"rel_side": args.rel_side} if args.workload.startswith("paper-") or
                       args.workload == "normal-1e7" else {}),
                    "reorder_queries": opts.get("reorder_queries", 2), "autotuned": tuned,
@@ -287,7 +295,7 @@ def run_ours(args, rank, world, local):
             "cover_cells": cell_stats["cells"], "cells_found_empty": cell_stats["empty"],
         },
     }
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and dim == 2:
         bopts = {"cover_refine": tuned["cover"], "occupancy_depth": args.occupancy, "query_norm": norm}
         if args.leaves is not None:
             bopts["leaves"] = args.leaves
@@ -327,6 +335,8 @@ def make_workload(args, rank):
         return workloads.mixed_1e8(scale=args.scale, seed=4 + 7919 * rank)
     if args.workload == "uniform-1e5":
         return workloads.uniform_1e5(scale=args.scale, seed=1 + 7919 * rank)
+    if args.workload == "mixed3d-1e7":
+        return workloads.mixed3d(scale=args.scale, seed=8 + 7919 * rank)
     if args.workload.startswith("paper-"):
         return workloads.paper_static(args.workload[6:], int(args.n), int(args.m), args.rel_side,
                                       seed=7 + 7919 * rank, scale=args.scale)
@@ -455,9 +465,10 @@ def e2e(sfc, torch, wl, total, bounds, args, cover):
     sfc_query_batch_host, host->device and device->host copies inside the timed region,
     inputs in pinned host memory."""
     n, m = wl.n, wl.m
-    hp = torch.empty((n, 2), dtype=torch.int32, pin_memory=True).numpy()
+    dim = wl.meta.get("dim", 2)
+    hp = torch.empty((n, dim), dtype=torch.int32, pin_memory=True).numpy()
     hp[:] = wl.points
-    hq = torch.empty((m, 2), dtype=torch.int32, pin_memory=True).numpy()
+    hq = torch.empty((m, dim), dtype=torch.int32, pin_memory=True).numpy()
     hq[:] = wl.queries
     hd = torch.empty(m, dtype=torch.int32, pin_memory=True).numpy()
     hd[:] = wl.delta
@@ -467,14 +478,17 @@ def e2e(sfc, torch, wl, total, bounds, args, cover):
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = sfc.sfc_build_host(hp, "z", bounds=bounds, cover_refine=cover, query_norm=wl.meta.get("norm", "disc"))
+        if dim == 3:
+            ix = sfc.sfc_build3_host(hp)
+        else:
+            ix = sfc.sfc_build_host(hp, "z", bounds=bounds, cover_refine=cover, query_norm=wl.meta.get("norm", "disc"))
         sfc.sfc_query_batch_host(ix, hq, hd, total, out_offsets=hoff, out_ids=hids)
         ix.close()
         torch.cuda.synchronize()
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
-    return {"value": m / t, "unit": UNIT, "h2d_bytes_per_step": n * 8 + m * 12,
+    return {"value": m / t, "unit": UNIT, "h2d_bytes_per_step": n * 4 * dim + m * 4 * (dim + 1),
             "d2h_bytes_per_step": (m + 1) * 8 + int(hoff[m]) * 4, "ms_per_step": t * 1e3}
 
 
@@ -488,7 +502,8 @@ def oracle_sample(wl, budget_s: float, threads: int):
     import oracle
 
     t0 = time.perf_counter()
-    idx = oracle.build(wl.points, 30, "z")
+    dim = wl.meta.get("dim", 2)
+    idx = oracle.build3(wl.points) if dim == 3 else oracle.build(wl.points, 30, "z")
     norm = wl.meta.get("norm", "disc")
     tb = time.perf_counter() - t0
     left = max(budget_s - tb, 1.0)
@@ -500,7 +515,10 @@ def oracle_sample(wl, budget_s: float, threads: int):
         if k <= 0:
             break
         t1 = time.perf_counter()
-        oracle.query(idx, wl.queries[done:done + k], wl.delta[done:done + k], threads=threads, norm=norm)
+        if dim == 3:   # the 3-D oracle runs on one thread
+            oracle.query3(idx, wl.queries[done:done + k], wl.delta[done:done + k])
+        else:
+            oracle.query(idx, wl.queries[done:done + k], wl.delta[done:done + k], threads=threads, norm=norm)
         tq += time.perf_counter() - t1
         done += k
         if tq > left:
@@ -515,6 +533,8 @@ def oracle_sample(wl, budget_s: float, threads: int):
 def cpu_baseline(wl, budget_s: float):
     threads = os.cpu_count() or 1
     v, det = oracle_sample(wl, budget_s, threads)
+    if wl.meta.get("dim", 2) == 3:
+        threads = 1
     return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": (f"oracle build (qsort, 1 thread) of all {wl.n} points + the first "
                        f"{det['queries_timed']} of {wl.m} queries on {threads} threads; "
@@ -526,7 +546,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = make_workload(args, 0)
-    threads = os.cpu_count() or 1
+    threads = 1 if wl.meta.get("dim", 2) == 3 else (os.cpu_count() or 1)
     vals = []
     det = None
     for i in range(args.warmup + args.steps):

@@ -121,6 +121,26 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
 sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, sfc_curve curve,
                           const sfc_options* opt, void* stream);
 
+/* 3-D index (the paper's d-dimensional Z curve, Sec. 2.1, for d = 3): d_points int32[n][3]
+ * with every coordinate in [0, 2^21); 63-bit keys (bit 3i = x_i, 3i + 1 = y_i, 3i + 2 = z_i);
+ * cells(Q) has at most 2^3 = 8 cells.  The query calls (sfc_query_count / _write / _batch /
+ * _batch_host, sfc_query_ranges, sfc_autotune, graphs, sfc_rebuild with int32[n][3] points)
+ * take int32[m][3] centres on such an index and report the closed ball
+ * dx^2 + dy^2 + dz^2 <= delta^2.  Static and with binary-search bounds only: opt->bounds must
+ * be SFC_BOUNDS_BINARY, cover_refine 0 (or -1), occupancy_depth 0, query_norm SFC_NORM_DISC
+ * (else SFC_ERR_INVALID); sfc_update, sfc_train_model, a learned bound search, finer covers
+ * and square windows return SFC_ERR_INVALID on it; queries run in input order. */
+sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt,
+                      void* stream);
+
+/* As sfc_build3 with the points in host memory (copied inside the call). */
+sfc_status sfc_build3_host(sfc_index** out, const int32_t* h_points, uint64_t n, const sfc_options* opt,
+                           void* stream);
+
+/* 2 for indexes made by sfc_build / sfc_build_host, 3 for sfc_build3 / sfc_build3_host; 0 for
+ * NULL. */
+int sfc_index_dim(const sfc_index* idx);
+
 /* Frees the index and everything it owns (stream-ordered on the stream of the last call). */
 void sfc_destroy(sfc_index* idx);
 
@@ -314,7 +334,8 @@ sfc_status sfc_update(sfc_index* idx, const int32_t* d_inserts, uint64_t k_ins,
 /* ---------------------------------------------------------------------------------- */
 
 /* Device views of the sorted arrays (owned by the index; valid until the next
- * sfc_update/sfc_destroy): keys uint64[n], ids uint32[n], xy int32[n][2]. */
+ * sfc_update/sfc_destroy): keys uint64[n], ids uint32[n], coordinates int32[n][2] (a 3-D
+ * index: int32[n][4] records x, y, z, 0). */
 sfc_status sfc_get_sorted(const sfc_index* idx, const uint64_t** d_keys, const uint32_t** d_ids,
                           const int32_t** d_xy, uint64_t* n);
 
@@ -326,6 +347,9 @@ sfc_status sfc_device_status(sfc_index* idx, uint32_t* h_bits, void* stream);
 /* Curve keys of n points (Alg. 2 for Z; the Hilbert labelling of Sec. 2.1), device in/out. */
 sfc_status sfc_keys(const int32_t* d_points, uint64_t n, sfc_curve curve, uint64_t* d_keys,
                     void* stream);
+
+/* 3-D Z keys (uint64[n], device) of int32[n][3] device points. */
+sfc_status sfc_keys3(const int32_t* d_points, uint64_t n, uint64_t* d_keys, void* stream);
 
 /* Inverse of sfc_keys: coordinates of n keys (device in/out). */
 sfc_status sfc_decode(const uint64_t* d_keys, uint64_t n, sfc_curve curve, int32_t* d_points,

@@ -88,6 +88,10 @@ def lib():
             "sfc_reserve_queries": (ci, [P, u64, P]),
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_set_cover": (ci, [P, ci]),
+            "sfc_build3": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
+            "sfc_build3_host": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
+            "sfc_index_dim": (ci, [P]),
+            "sfc_keys3": (ci, [P, u64, P, P]),
             "sfc_set_query_norm": (ci, [P, ci]),
             "sfc_get_occupancy": (ci, [P, P, u64, P, P]),
             "sfc_query_cell_stats": (ci, [P, P, P, P]),
@@ -173,8 +177,8 @@ def _bounds(b):
     raise ValueError(f"unknown bounds mode {b!r}")
 
 
-def _pts(t):
-    assert t.dtype == torch.int32 and t.dim() == 2 and t.shape[1] == 2, "points must be int32 [n, 2]"
+def _pts(t, dim: int = 2):
+    assert t.dtype == torch.int32 and t.dim() == 2 and t.shape[1] == dim, f"points must be int32 [n, {dim}]"
     return t.contiguous()
 
 
@@ -224,10 +228,11 @@ def sfc_launch_count() -> int:
 class Index:
     """Owns an sfc_index handle."""
 
-    def __init__(self, handle: ctypes.c_void_p, curve: int, device):
+    def __init__(self, handle: ctypes.c_void_p, curve: int, device, dim: int = 2):
         self._h = handle
         self.curve = curve
         self.device = device
+        self.dim = dim
 
     @property
     def handle(self):
@@ -265,12 +270,39 @@ def sfc_build_host(points: np.ndarray, curve="z", options: sfc_options | None = 
     return Index(h, _curve(curve), torch.device("cuda", torch.cuda.current_device()))
 
 
+def sfc_build3(points: torch.Tensor, options: sfc_options | None = None, stream=None, **opts) -> Index:
+    """3-D index of int32 [n, 3] points (Z curve in Z^3, coordinates in [0, 2^21))."""
+    points = _pts(points, 3)
+    o = options if options is not None else sfc_default_options(**opts)
+    h = ctypes.c_void_p()
+    _check(lib().sfc_build3(ctypes.byref(h), _dptr(points), points.shape[0], ctypes.byref(o), _stream(stream)),
+           "sfc_build3")
+    return Index(h, SFC_CURVE_Z, points.device, dim=3)
+
+
+def sfc_build3_host(points: np.ndarray, options: sfc_options | None = None, stream=None, **opts) -> Index:
+    points = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 3)
+    o = options if options is not None else sfc_default_options(**opts)
+    h = ctypes.c_void_p()
+    _check(lib().sfc_build3_host(ctypes.byref(h), _hptr(points), points.shape[0], ctypes.byref(o),
+                                 _stream(stream)), "sfc_build3_host")
+    return Index(h, SFC_CURVE_Z, torch.device("cuda", torch.cuda.current_device()), dim=3)
+
+
+def sfc_keys3(points: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    points = _pts(points, 3)
+    if out is None:
+        out = torch.empty(points.shape[0], dtype=torch.int64, device=points.device)
+    _check(lib().sfc_keys3(_dptr(points), points.shape[0], _dptr(out), _stream(stream)), "sfc_keys3")
+    return out
+
+
 def sfc_destroy(index: Index):
     index.close()
 
 
 def sfc_rebuild(index: Index, points: torch.Tensor, stream=None):
-    points = _pts(points)
+    points = _pts(points, index.dim)
     _check(lib().sfc_rebuild(index.handle, _dptr(points), points.shape[0], _stream(stream)), "sfc_rebuild")
 
 
@@ -320,7 +352,7 @@ def sfc_graph_capture(index: Index, points: torch.Tensor | None, q: torch.Tensor
 
 def sfc_query_count(index: Index, q: torch.Tensor, delta: torch.Tensor,
                     out_offsets: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    q = _pts(q)
+    q = _pts(q, index.dim)
     delta = delta.contiguous()
     m = q.shape[0]
     if out_offsets is None:
@@ -341,7 +373,7 @@ def sfc_query_write(index: Index, q: torch.Tensor, delta: torch.Tensor, out_offs
 
 def sfc_query_batch(index: Index, q: torch.Tensor, delta: torch.Tensor, out_offsets: torch.Tensor,
                     out_ids: torch.Tensor, capacity: int | None = None, stream=None):
-    q = _pts(q)
+    q = _pts(q, index.dim)
     delta = delta.contiguous()
     cap = out_ids.numel() if capacity is None else int(capacity)
     _check(lib().sfc_query_batch(index.handle, _dptr(q), _dptr(delta), q.shape[0], _dptr(out_offsets),
@@ -352,7 +384,7 @@ def sfc_query_batch(index: Index, q: torch.Tensor, delta: torch.Tensor, out_offs
 
 def query(index: Index, q: torch.Tensor, delta: torch.Tensor, stream=None):
     """Count, read the total, allocate, write: returns (offsets int64[m+1], ids int32[total])."""
-    q = _pts(q)
+    q = _pts(q, index.dim)
     delta = delta.contiguous()
     off = sfc_query_count(index, q, delta, stream=stream)
     total = int(off[-1].item())
@@ -364,7 +396,7 @@ def query(index: Index, q: torch.Tensor, delta: torch.Tensor, stream=None):
 def sfc_query_batch_host(index: Index, q: np.ndarray, delta: np.ndarray, capacity: int,
                          out_offsets: np.ndarray | None = None, out_ids: np.ndarray | None = None,
                          stream=None):
-    q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1, 2)
+    q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1, index.dim)
     delta = np.ascontiguousarray(delta, dtype=np.int32).reshape(-1)
     m = q.shape[0]
     if out_offsets is None:
@@ -378,7 +410,7 @@ def sfc_query_batch_host(index: Index, q: np.ndarray, delta: np.ndarray, capacit
 
 
 def sfc_autotune(index: Index, q: torch.Tensor, delta: torch.Tensor, force: bool = False, stream=None) -> dict:
-    q = _pts(q)
+    q = _pts(q, index.dim)
     delta = delta.contiguous()
     c, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().sfc_autotune(index.handle, _dptr(q), _dptr(delta), q.shape[0], int(bool(force)), ctypes.byref(c),
@@ -530,20 +562,22 @@ def sfc_update(index: Index, inserts: torch.Tensor | None, delete_ids: torch.Ten
 
 
 def sfc_get_sorted(index: Index, copy: bool = True):
-    """(keys int64[n], ids int32[n], xy int32[n, 2]) of the sorted array."""
+    """(keys int64[n], ids int32[n], coordinates int32[n, 2] or, for a 3-D index, int32[n, 4]
+    records x, y, z, 0) of the sorted array."""
     k, i, x = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     n = ctypes.c_uint64()
     _check(lib().sfc_get_sorted(index.handle, ctypes.byref(k), ctypes.byref(i), ctypes.byref(x),
                                 ctypes.byref(n)), "sfc_get_sorted")
     n = n.value
     dev = index.device
+    c = 4 if index.dim == 3 else 2
     if n == 0:
         return (torch.empty(0, dtype=torch.int64, device=dev), torch.empty(0, dtype=torch.int32, device=dev),
-                torch.empty((0, 2), dtype=torch.int32, device=dev))
+                torch.empty((0, c), dtype=torch.int32, device=dev))
     with torch.cuda.device(dev):
         kt = torch.as_tensor(_CudaView(k.value, (n,), "<i8"), device=dev)
         it = torch.as_tensor(_CudaView(i.value, (n,), "<i4"), device=dev)
-        xt = torch.as_tensor(_CudaView(x.value, (n, 2), "<i4"), device=dev)
+        xt = torch.as_tensor(_CudaView(x.value, (n, c), "<i4"), device=dev)
     if copy:
         return kt.clone(), it.clone(), xt.clone()
     return kt, it, xt
@@ -602,7 +636,7 @@ def sfc_exclusive_scan_noalloc(x: torch.Tensor, out: torch.Tensor | None = None,
 
 
 def sfc_query_ranges(index: Index, q: torch.Tensor, delta: torch.Tensor, stream=None):
-    q = _pts(q)
+    q = _pts(q, index.dim)
     delta = delta.contiguous()
     m = q.shape[0]
     dev = q.device

@@ -123,6 +123,28 @@ sfc_status build_from_device(sfc_index* idx, const int32_t* d_points, cudaStream
     return SFC_OK;
 }
 
+// 3-D: keys of the input points, the (key, id) sort, and the coordinates decoded from the sorted
+// keys into 16-byte records.
+sfc_status build3_from_device(sfc_index* idx, const int32_t* d_points, cudaStream_t st)
+{
+    const uint64_t n = idx->n;
+    SFC_TRY(idx->keys.ensure(n * sizeof(uint64_t), st));
+    SFC_TRY(idx->ids.ensure(n * sizeof(uint32_t), st));
+    SFC_TRY(idx->xyz.ensure(n * sizeof(int4), st));
+    SFC_TRY(idx->keys_in.ensure(n * sizeof(uint64_t), st));
+    ProfScope ps(idx, "sort", st);
+    SFC_TRY(launch_keys3(d_points, n, idx->keys_in.as<uint64_t>(), status_word(idx), st));
+    SortSource src;
+    src.keys = idx->keys_in.as<uint64_t>();
+    SortDest dst;
+    dst.keys = idx->keys.as<uint64_t>();
+    dst.vals = idx->ids.as<uint32_t>();
+    SFC_TRY(radix_sort(src, n, dst, idx->sort_ws, status_word(idx), st));
+    SFC_TRY(launch_decode3(idx->keys.as<uint64_t>(), n, idx->xyz.as<int4>(), st));
+    idx->next_id = (uint32_t)n;
+    return SFC_OK;
+}
+
 QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint64_t m)
 {
     QueryArgs a{};
@@ -136,8 +158,10 @@ QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint
     a.m = m;
     a.status = status_word(idx);
     a.drop = idx->drop;
-    a.kint = (uint32_t)cover_intervals(idx->drop);
+    a.kint = (uint32_t)query_intervals(idx->dim, idx->drop);
     a.norm = idx->norm;
+    a.dim = idx->dim;
+    a.xyz = idx->xyz.as<int4>();
     if (idx->opt.occupancy_depth > 0 && idx->occ.ptr) {
         a.occ = idx->occ.as<uint32_t>();
         a.occ_depth = idx->opt.occupancy_depth;
@@ -149,12 +173,12 @@ QueryArgs base_args(sfc_index* idx, const int32_t* q, const int32_t* delta, uint
 sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
 {
     QueryWs& w = idx->qws;
-    SFC_TRY(w.ranges.ensure(m * 2 * cover_intervals(idx->drop) * sizeof(uint32_t), st));
+    SFC_TRY(w.ranges.ensure(m * 2 * query_intervals(idx->dim, idx->drop) * sizeof(uint32_t), st));
     SFC_TRY(w.nchunks.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
-    if (idx->opt.reorder_queries != 0) {
+    if (idx->opt.reorder_queries != 0 && idx->dim == 2) {
         SFC_TRY(w.qkeys.ensure(m * sizeof(uint64_t), st));
         SFC_TRY(w.qkeys_sorted.ensure(m * sizeof(uint64_t), st));
         SFC_TRY(w.perm.ensure(m * sizeof(uint32_t), st));
@@ -184,7 +208,7 @@ const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
 // 128 MB of coordinates); option 1 forces it, 0 disables it.
 bool use_curve_order(const sfc_index* idx, uint64_t m)
 {
-    if (m < 2 || idx->opt.reorder_queries == 0) return false;
+    if (m < 2 || idx->opt.reorder_queries == 0 || idx->dim != 2) return false;
     if (idx->opt.reorder_queries == 1) return true;
     return idx->n >= (1ull << 24);
 }
@@ -270,7 +294,7 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     if (m == 0) return SFC_OK;
     QueryArgs a = base_args(idx, d_q, d_delta, m);
     a.drop = w.pending.drop;
-    a.kint = (uint32_t)cover_intervals(a.drop);
+    a.kint = (uint32_t)query_intervals(idx->dim, a.drop);
     a.norm = w.pending.norm;
     a.ranges = w.ranges.as<uint32_t>();
     a.nchunks = w.nchunks.as<uint32_t>();
@@ -399,6 +423,7 @@ sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void
     idx->qws.pending.valid = false;
     SFC_TRY(ensure_status_buf(idx, st));
     // every issued id is live again
+    if (idx->dim == 3) return build3_from_device(idx, d_points, st);
     if (idx->alive.ptr) SFC_CUDA_TRY(cudaMemsetAsync(idx->alive.ptr, 0xff, idx->alive.bytes, st));
     SFC_TRY(build_from_device(idx, d_points, st));
     if (idx->opt.bounds == SFC_BOUNDS_LEARNED) {
@@ -416,9 +441,14 @@ sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* str
     const uint64_t n1 = n_max ? n_max : 1;
     SFC_TRY(idx->keys.ensure(n1 * sizeof(uint64_t), st));
     SFC_TRY(idx->ids.ensure(n1 * sizeof(uint32_t), st));
-    SFC_TRY(idx->xy.ensure(n1 * sizeof(int2), st));
-    SFC_TRY(idx->xy_by_id.ensure(n1 * sizeof(int2), st));
-    SFC_TRY(ensure_alive_bits(idx, n1, st));
+    if (idx->dim == 3) {
+        SFC_TRY(idx->xyz.ensure(n1 * sizeof(int4), st));
+        SFC_TRY(idx->keys_in.ensure(n1 * sizeof(uint64_t), st));
+    } else {
+        SFC_TRY(idx->xy.ensure(n1 * sizeof(int2), st));
+        SFC_TRY(idx->xy_by_id.ensure(n1 * sizeof(int2), st));
+        SFC_TRY(ensure_alive_bits(idx, n1, st));
+    }
     if (idx->opt.occupancy_depth > 0)
         SFC_TRY(idx->occ.ensure(occupancy_words(idx->opt.occupancy_depth) * sizeof(uint32_t), st));
     SFC_TRY(reserve_sort(idx->sort_ws, n1, st));
@@ -671,13 +701,14 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
 sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm)
 {
     if (!idx || (norm != SFC_NORM_DISC && norm != SFC_NORM_SQUARE)) return SFC_ERR_INVALID;
+    if (idx->dim == 3 && norm != SFC_NORM_DISC) return SFC_ERR_INVALID;
     idx->norm = norm;
     return SFC_OK;
 }
 
 sfc_status sfc_set_cover(sfc_index* idx, int refine)
 {
-    if (!idx || refine < 0 || refine > 2) return SFC_ERR_INVALID;
+    if (!idx || refine < 0 || refine > 2 || (idx->dim == 3 && refine != 0)) return SFC_ERR_INVALID;
     idx->drop = refine;
     return SFC_OK;
 }
@@ -709,7 +740,7 @@ sfc_status sfc_query_cell_stats(const sfc_index* cidx, uint64_t* h_cells, uint64
     return SFC_OK;
 }
 
-int sfc_query_max_intervals(const sfc_index* idx) { return idx ? cover_intervals(idx->drop) : 0; }
+int sfc_query_max_intervals(const sfc_index* idx) { return idx ? query_intervals(idx->dim, idx->drop) : 0; }
 
 int sfc_cover_refine(const sfc_index* idx) { return idx ? idx->drop : -1; }
 
@@ -723,14 +754,15 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
     cudaStream_t st = as_stream(stream);
     idx->last_stream = st;
     HostStage& hs = idx->stage;
-    SFC_TRY(hs.q.ensure(m * sizeof(int2), st));
+    const uint64_t qbytes = m * (uint64_t)idx->dim * sizeof(int32_t);
+    SFC_TRY(hs.q.ensure(qbytes, st));
     SFC_TRY(hs.delta.ensure(m * sizeof(int32_t), st));
     SFC_TRY(hs.offsets.ensure((m + 1) * sizeof(uint64_t), st));
     int32_t* dq = hs.q.as<int32_t>();
     int32_t* dd = hs.delta.as<int32_t>();
     uint64_t* doff = hs.offsets.as<uint64_t>();
     if (m) {
-        SFC_CUDA_TRY(cudaMemcpyAsync(dq, h_q, m * sizeof(int2), cudaMemcpyHostToDevice, st));
+        SFC_CUDA_TRY(cudaMemcpyAsync(dq, h_q, qbytes, cudaMemcpyHostToDevice, st));
         SFC_CUDA_TRY(cudaMemcpyAsync(dd, h_delta, m * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     }
     SFC_TRY(do_count(idx, dq, dd, m, doff, st));
@@ -759,6 +791,7 @@ sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream)
 sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode)
 {
     if (!idx || (mode != SFC_BOUNDS_BINARY && mode != SFC_BOUNDS_LEARNED)) return SFC_ERR_INVALID;
+    if (idx->dim == 3 && mode != SFC_BOUNDS_BINARY) return SFC_ERR_INVALID;
     if (mode == SFC_BOUNDS_LEARNED && !idx->model.trained) return SFC_ERR_STATE;
     idx->bounds = mode;
     return SFC_OK;
@@ -766,7 +799,7 @@ sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode)
 
 sfc_status sfc_train_model(sfc_index* idx, void* stream)
 {
-    if (!idx) return SFC_ERR_INVALID;
+    if (!idx || idx->dim != 2) return SFC_ERR_INVALID;
     idx->last_stream = as_stream(stream);
     ProfScope ps(idx, "train", as_stream(stream));
     return train_model(idx, as_stream(stream));
@@ -857,9 +890,67 @@ sfc_status sfc_get_sorted(const sfc_index* idx, const uint64_t** d_keys, const u
     if (!idx) return SFC_ERR_INVALID;
     if (d_keys) *d_keys = idx->keys.as<uint64_t>();
     if (d_ids) *d_ids = idx->ids.as<uint32_t>();
-    if (d_xy) *d_xy = idx->xy.as<int32_t>();
+    if (d_xy) *d_xy = idx->dim == 3 ? idx->xyz.as<int32_t>() : idx->xy.as<int32_t>();
     if (n) *n = idx->n;
     return SFC_OK;
+}
+
+int sfc_index_dim(const sfc_index* idx) { return idx ? idx->dim : 0; }
+
+sfc_status sfc_keys3(const int32_t* d_points, uint64_t n, uint64_t* d_keys, void* stream)
+{
+    if (n && (!d_points || !d_keys)) return SFC_ERR_INVALID;
+    return launch_keys3(d_points, n, d_keys, nullptr, as_stream(stream));
+}
+
+sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt, void* stream)
+{
+    if (!out) return SFC_ERR_INVALID;
+    *out = nullptr;
+    if (n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
+    sfc_options o;
+    sfc_default_options(&o);
+    if (opt) o = *opt;
+    if (o.bounds != SFC_BOUNDS_BINARY || o.cover_refine > 0 || o.occupancy_depth != 0 ||
+        o.query_norm != SFC_NORM_DISC || o.mask_budget_mb < 1 ||
+        (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))))
+        return SFC_ERR_INVALID;
+    o.cover_refine = 0;
+    o.reorder_queries = 0;
+    cudaStream_t st = as_stream(stream);
+    sfc_index* idx = new (std::nothrow) sfc_index();
+    if (!idx) return SFC_ERR_OOM;
+    cudaGetDevice(&idx->device);
+    idx->curve = SFC_CURVE_Z;
+    idx->dim = 3;
+    idx->n = n;
+    idx->opt = o;
+    idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;
+    idx->last_stream = st;
+    idx->prof.on = o.profile != 0;
+    sfc_status s = ensure_status_buf(idx, st);
+    if (s == SFC_OK) s = build3_from_device(idx, d_points, st);
+    if (s != SFC_OK) {
+        sfc_destroy(idx);
+        return s;
+    }
+    *out = idx;
+    return SFC_OK;
+}
+
+sfc_status sfc_build3_host(sfc_index** out, const int32_t* h_points, uint64_t n, const sfc_options* opt,
+                           void* stream)
+{
+    if (!out) return SFC_ERR_INVALID;
+    *out = nullptr;
+    if (n >= 0xffffffffull || (n && !h_points)) return SFC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    void* d = nullptr;
+    SFC_TRY(dev_alloc(&d, n * 3 * sizeof(int32_t), st));
+    cudaError_t e = n ? cudaMemcpyAsync(d, h_points, n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st) : cudaSuccess;
+    sfc_status s = e == cudaSuccess ? sfc_build3(out, static_cast<int32_t*>(d), n, opt, stream) : SFC_ERR_CUDA;
+    dev_free(d, st);
+    return s;
 }
 
 sfc_status sfc_device_status(sfc_index* idx, uint32_t* h_bits, void* stream)

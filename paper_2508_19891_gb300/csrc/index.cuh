@@ -71,6 +71,7 @@ struct sfc_index {
     uint32_t qbatch = 8;                // queries per write-queue grab
     int drop = 0;                       // cover refinement: levels below cells(Q) (0..2)
     int norm = 0;                       // query window (sfc_norm)
+    int dim = 2;                        // 2, or 3 for indexes made by sfc_build3
     cudaStream_t last_stream = nullptr;
 
     sfc::DevBuf keys, ids, xy;          // the sorted array A_P and its keys
@@ -78,6 +79,8 @@ struct sfc_index {
     sfc::DevBuf alive;                  // liveness bitmap by id
     sfc::DevBuf status;                 // device status word + model statistics
     sfc::DevBuf occ;                    // early-termination bitmap (occupancy_depth > 0)
+    sfc::DevBuf xyz;                    // 3-D: coordinates in sorted order (int4 x, y, z, 0)
+    sfc::DevBuf keys_in;                // 3-D: keys in input order (the sort's source)
 
     sfc::SortWorkspace sort_ws;
     sfc::ScanWorkspace scan_ws;

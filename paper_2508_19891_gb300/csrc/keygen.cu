@@ -67,6 +67,31 @@ __global__ void __launch_bounds__(kThreads) decode_kernel(const uint64_t* __rest
     }
 }
 
+// 3-D Z keys: points are 12-byte records, read as three 32-bit words (consecutive threads read
+// consecutive records, so a warp's loads cover 384 contiguous bytes).
+__global__ void __launch_bounds__(kThreads) keys3_kernel(const int32_t* __restrict__ pts, uint64_t n,
+                                                         uint64_t* __restrict__ keys, uint32_t* status)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
+        bad |= !point3_in_domain(x, y, z);
+        keys[i] = morton3_key((uint32_t)x, (uint32_t)y, (uint32_t)z);
+    }
+    if (bad) set_status(status, SFC_DEV_BAD_POINT);
+}
+
+__global__ void __launch_bounds__(kThreads) decode3_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+                                                           int4* __restrict__ xyz)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+        xyz[i] = make_int4((int)gather3_bits(k), (int)gather3_bits(k >> 1), (int)gather3_bits(k >> 2), 0);
+    }
+}
+
 int grid_for(uint64_t work, int per_block)
 {
     uint64_t want = (work + per_block - 1) / per_block;
@@ -100,6 +125,22 @@ sfc_status launch_decode(const uint64_t* keys, uint64_t n, int curve, int2* pts,
         decode_kernel<SFC_CURVE_HILBERT><<<g, kThreads, 0, st>>>(keys, n, pts);
     else
         decode_kernel<SFC_CURVE_Z><<<g, kThreads, 0, st>>>(keys, n, pts);
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_keys3(const int32_t* pts, uint64_t n, uint64_t* keys, uint32_t* status, cudaStream_t st)
+{
+    if (n == 0) return SFC_OK;
+    keys3_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(pts, n, keys, status);
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_decode3(const uint64_t* keys, uint64_t n, int4* xyz, cudaStream_t st)
+{
+    if (n == 0) return SFC_OK;
+    decode3_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(keys, n, xyz);
     count_launch();
     return launch_status();
 }

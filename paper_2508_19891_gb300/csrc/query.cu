@@ -360,6 +360,121 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
 }
 
 // ------------------------------------------------------------------------------------
+// plan3_kernel: the same for 3-D points (Z curve in Z^3, binary bound search)
+// ------------------------------------------------------------------------------------
+constexpr int kCells3 = 8;   // cells(Q) in 3-D: at most two per axis
+
+// cells(Q) in 3-D: the cells of level l (2 delta <= 2^l < 4 delta, capped at 21) meeting the
+// clipped cube Q, key intervals of length 8^l, sorted, abutting ones merged.
+__device__ __forceinline__ int derive_ranges3(int32_t qx, int32_t qy, int32_t qz, int32_t delta, uint64_t* lo,
+                                              uint64_t* hi)
+{
+    const int64_t d = delta;
+    const int64_t c[3] = {qx, qy, qz};
+    int64_t a0[3], a1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a0[k] = max((int64_t)0, c[k] - d);
+        a1[k] = min((int64_t)kSide3 - 1, c[k] + d);
+    }
+    int l = 0;
+    if (d > 0) {
+        l = 64 - __clzll((unsigned long long)(2 * d - 1));
+        if (l > kOmega3) l = kOmega3;
+    }
+    const uint64_t span = (1ull << (3 * l)) - 1;   // 3 l <= 63
+    int cnt = 0;
+    for (int64_t cz = a0[2] >> l; cz <= (a1[2] >> l); ++cz)
+        for (int64_t cy = a0[1] >> l; cy <= (a1[1] >> l); ++cy)
+            for (int64_t cx = a0[0] >> l; cx <= (a1[0] >> l); ++cx) {
+                if (cnt == kCells3) break;   // unreachable: at most two cells per axis
+                const uint64_t k0 = morton3_key((uint32_t)(cx << l), (uint32_t)(cy << l), (uint32_t)(cz << l)) & ~span;
+                int j = cnt;
+                while (j > 0 && lo[j - 1] > k0) { lo[j] = lo[j - 1]; hi[j] = hi[j - 1]; --j; }
+                lo[j] = k0;
+                hi[j] = k0 | span;
+                ++cnt;
+            }
+    int m = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (m > 0 && hi[m - 1] + 1 == lo[i]) {
+            hi[m - 1] = hi[i];
+        } else {
+            lo[m] = lo[i];
+            hi[m] = hi[i];
+            ++m;
+        }
+    }
+    return m;
+}
+
+template <bool EXPORT>
+__global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExport ex)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = i < a.m;
+    int32_t qx = 0, qy = 0, qz = 0, delta = -1;
+    if (active) {
+        qx = __ldg(a.q + 3 * i);
+        qy = __ldg(a.q + 3 * i + 1);
+        qz = __ldg(a.q + 3 * i + 2);
+        delta = __ldg(a.delta + i);
+    }
+    const bool ok = active && point3_in_domain(qx, qy, qz) && delta >= 0;
+    if (active && !ok) set_status(a.status, SFC_DEV_BAD_QUERY);
+    uint64_t lo[kCells3], hi[kCells3];
+    uint32_t b[kCells3], e[kCells3];
+    const int cnt = ok ? derive_ranges3(qx, qy, qz, delta, lo, hi) : 0;
+    BoundStats bs;
+    const BinaryBounds bounds{};
+#pragma unroll 1
+    for (int bi = 0; bi < 2 && 8 * bi < 2 * cnt; ++bi) {
+        uint64_t t[8];
+        uint32_t r[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int ep = 8 * bi + x;
+            t[x] = ep < 2 * cnt ? ((ep & 1) ? hi[ep >> 1] + 1 : lo[ep >> 1]) : 0;
+        }
+        bounds.search<8>(a.keys, a.n, t, r, min(2 * cnt - 8 * bi, 8), bs);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int ep = 8 * bi + x;
+            if (ep < 2 * cnt) {
+                if (ep & 1) e[ep >> 1] = r[x];
+                else b[ep >> 1] = r[x];
+            }
+        }
+    }
+    uint64_t S = 0;
+    for (int k = 0; k < cnt; ++k) S += e[k] - b[k];
+    if (!EXPORT) {   // statistics: one atomic per warp and counter
+        const unsigned long long ts = warp_sum_u64(S), tc = warp_sum_u64((unsigned long long)cnt);
+        if (lane_id() == 0) {
+            if (a.scanned && ts) atomicAdd(a.scanned, ts);
+            if (a.cells && tc) atomicAdd(a.cells, tc);
+        }
+    }
+    if (!active) return;
+    if (!EXPORT) {
+        uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * kCells3 * i);
+#pragma unroll
+        for (int k = 0; k < kCells3; ++k) rp[k] = k < cnt ? make_uint2(b[k], e[k]) : make_uint2(0u, 0u);
+        a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+    } else {
+        for (int k = 0; k < kCells3; ++k) {
+            const bool u = k < cnt;
+            const uint64_t o = (uint64_t)kCells3 * i + k;
+            if (ex.lo) ex.lo[o] = u ? lo[k] : 1;
+            if (ex.hi) ex.hi[o] = u ? hi[k] : 0;
+            if (ex.b) ex.b[o] = u ? b[k] : 0;
+            if (ex.e) ex.e[o] = u ? e[k] : 0;
+        }
+        if (ex.cnt) ex.cnt[i] = (uint32_t)cnt;
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Shared helpers of the two scan passes
 // ------------------------------------------------------------------------------------
 constexpr int kMaxInt = 25;   // intervals per query at the finest cover
@@ -375,6 +490,7 @@ struct QView {
     uint32_t S;      // concatenated length (sum of the interval lengths)
     uint32_t nint;   // intervals stored per query
     int2 q;
+    int32_t qz;      // third coordinate of 3-D queries
     int32_t d;       // delta
     int64_t d2;      // delta^2
 };
@@ -410,7 +526,13 @@ __device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi, War
     __syncwarp();
     v.S = __shfl_sync(0xffffffffu, incl, 31);
     v.nint = a.kint;
-    v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
+    if (a.dim == 3) {
+        v.q = make_int2(__ldg(a.q + 3 * qi), __ldg(a.q + 3 * qi + 1));
+        v.qz = __ldg(a.q + 3 * qi + 2);
+    } else {
+        v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
+        v.qz = 0;
+    }
     v.d = __ldg(a.delta + qi);
     v.d2 = (int64_t)v.d * v.d;
     return v;
@@ -425,15 +547,43 @@ __device__ __forceinline__ void seek(const WarpTab* tab, uint32_t nint, uint32_t
     end = tab->end[r];
 }
 
+// The scans are specialised by geometry: the 2-D disc, the 2-D square window, and the 3-D
+// ball (points stored as 16-byte int4 records).
+constexpr int kGeomDisc = SFC_NORM_DISC;
+constexpr int kGeomSquare = SFC_NORM_SQUARE;
+constexpr int kGeomBall3 = 2;
+
+template <int GEOM>
+struct Geom {
+    using P = int2;
+    static __device__ __forceinline__ const P* points(const QueryArgs& a) { return a.xy; }
+    static __device__ __forceinline__ P zero() { return make_int2(0, 0); }
+};
+template <>
+struct Geom<kGeomBall3> {
+    using P = int4;
+    static __device__ __forceinline__ const P* points(const QueryArgs& a) { return a.xyz; }
+    static __device__ __forceinline__ P zero() { return make_int4(0, 0, 0, 0); }
+};
+
 // Exact window tests.  Disc (the problem statement's closed ball): |dx|, |dy| < 2^30, so each
 // square is one signed 32x32 -> 64-bit multiply(-add) and the sum stays below 2^61.  Square
-// (the experiments' windows): max(|dx|, |dy|) <= delta in 32-bit integers.
-template <int NORM>
+// (the experiments' windows): max(|dx|, |dy|) <= delta in 32-bit integers.  3-D ball:
+// |dx|, |dy|, |dz| < 2^21, the sum of squares stays below 2^44.
+template <int GEOM>
 __device__ __forceinline__ bool is_hit(const QView& v, int2 p)
 {
     const int dx = p.x - v.q.x, dy = p.y - v.q.y;
-    if (NORM == SFC_NORM_SQUARE) return max(abs(dx), abs(dy)) <= v.d;
+    if (GEOM == kGeomSquare) return max(abs(dx), abs(dy)) <= v.d;
     const long long s = (long long)dx * dx + (long long)dy * dy;
+    return s <= v.d2;
+}
+
+template <int GEOM>
+__device__ __forceinline__ bool is_hit(const QView& v, int4 p)
+{
+    const int dx = p.x - v.q.x, dy = p.y - v.q.y, dz = p.z - v.qz;
+    const long long s = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
     return s <= v.d2;
 }
 
@@ -458,40 +608,41 @@ __device__ __forceinline__ void keep_words(uint32_t (&words)[WPL], uint32_t it, 
 // groups of 4 x 32: when the whole group lies inside the chunk and no lane crosses the end of
 // its interval (one vote), the group runs without per-point guards; otherwise each point is
 // checked and the lane looks its interval up again when it crosses into the next one.
-template <int WPL, int NORM>
+template <int WPL, int GEOM>
 __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, const WarpTab* tab,
                                                  uint32_t s0, uint32_t s1, uint32_t (&words)[WPL])
 {
 #pragma unroll
     for (int s = 0; s < WPL; ++s) words[s] = 0;
     const uint32_t nit = (s1 - s0 + 31) >> 5;
-    const int2* __restrict__ xy = a.xy;
+    using P = typename Geom<GEOM>::P;
+    const P* __restrict__ xy = Geom<GEOM>::points(a);
     uint32_t f = s0 + lane_id();
     uint32_t r = 0, shift, end;
     seek(tab, v.nint, f, r, shift, end);
     for (uint32_t it = 0; it < nit; it += 4, f += 128) {
         const bool full = s0 + (it + 4) * 32 <= s1;     // warp-uniform
         if (full && __all_sync(0xffffffffu, f + 96 < end)) {
-            const int2* p = xy + (f + shift);
-            const int2 p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
-            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p0));
-            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p1));
-            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p2));
-            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit<NORM>(v, p3));
+            const P* p = xy + (f + shift);
+            const P p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
+            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p0));
+            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p1));
+            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p2));
+            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p3));
             keep_words<WPL>(words, it, w0, w1, w2, w3);
         } else {
-            int2 p[4];
+            P p[4];
             bool val[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const uint32_t fu = f + 32u * u;
                 val[u] = fu < s1;
                 if (fu >= end) seek(tab, v.nint, fu, r, shift, end);
-                p[u] = val[u] ? __ldg(xy + (fu + shift)) : make_int2(0, 0);
+                p[u] = val[u] ? __ldg(xy + (fu + shift)) : Geom<GEOM>::zero();
             }
             uint32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit<NORM>(v, p[u]));
+            for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit<GEOM>(v, p[u]));
             keep_words<WPL>(words, it, w[0], w[1], w[2], w[3]);
         }
     }
@@ -525,7 +676,7 @@ __device__ __forceinline__ uint64_t owner_query(const uint64_t* __restrict__ bas
 // ------------------------------------------------------------------------------------
 // count_kernel
 // ------------------------------------------------------------------------------------
-template <int WPL, int NORM>
+template <int WPL, int GEOM>
 __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 {
     __shared__ WarpTab s_tab[kThreads / 32];
@@ -556,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
             const uint32_t s0 = j * a.chunk;
             const uint32_t s1 = min(v.S, s0 + a.chunk);
             uint32_t words[WPL];
-            const uint32_t cnt = filter_chunk<WPL, NORM>(a, v, tab, s0, s1, words);
+            const uint32_t cnt = filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words);
             if (g < a.mask_chunks) {
                 const uint32_t nw = (s1 - s0 + 31) >> 5;
                 uint32_t* mp = a.masks + g * W;
@@ -574,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 // ------------------------------------------------------------------------------------
 // write_kernel
 // ------------------------------------------------------------------------------------
-template <int WPL, int NORM>
+template <int WPL, int GEOM>
 __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
 {
     // per-warp staging of the array positions of one group of 32 mask words (<= 1024 hits)
@@ -616,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                         words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
                     }
                 } else {
-                    filter_chunk<WPL, NORM>(a, v, tab, s0, s1, words);
+                    filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words);
                 }
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
@@ -683,23 +834,24 @@ int persistent_grid(const void* fn)
     return per_sm * num_sms();
 }
 
-template <int WPL, int NORM>
-void launch_count_write_norm(const QueryArgs& a, bool write, cudaStream_t st)
+template <int WPL, int GEOM>
+void launch_count_write_geom(const QueryArgs& a, bool write, cudaStream_t st)
 {
     if (!write) {
-        int g = persistent_grid((const void*)count_kernel<WPL, NORM>);
-        count_kernel<WPL, NORM><<<g, kThreads, 0, st>>>(a);
+        int g = persistent_grid((const void*)count_kernel<WPL, GEOM>);
+        count_kernel<WPL, GEOM><<<g, kThreads, 0, st>>>(a);
     } else {
-        int g = persistent_grid((const void*)write_kernel<WPL, NORM>);
-        write_kernel<WPL, NORM><<<g, kThreads, 0, st>>>(a);
+        int g = persistent_grid((const void*)write_kernel<WPL, GEOM>);
+        write_kernel<WPL, GEOM><<<g, kThreads, 0, st>>>(a);
     }
 }
 
 template <int WPL>
 sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 {
-    if (a.norm == SFC_NORM_SQUARE) launch_count_write_norm<WPL, SFC_NORM_SQUARE>(a, write, st);
-    else launch_count_write_norm<WPL, SFC_NORM_DISC>(a, write, st);
+    if (a.dim == 3) launch_count_write_geom<WPL, kGeomBall3>(a, write, st);
+    else if (a.norm == SFC_NORM_SQUARE) launch_count_write_geom<WPL, kGeomSquare>(a, write, st);
+    else launch_count_write_geom<WPL, kGeomDisc>(a, write, st);
     count_launch();
     return launch_status();
 }
@@ -721,6 +873,11 @@ template <bool EXPORT>
 static sfc_status plan_launch(const QueryArgs& a, const LearnedModelView* lm, const PlanExport& ex, cudaStream_t st)
 {
     if (a.m == 0) return SFC_OK;
+    if (a.dim == 3) {
+        plan3_kernel<EXPORT><<<(unsigned)((a.m + kThreads - 1) / kThreads), kThreads, 0, st>>>(a, ex);
+        count_launch();
+        return launch_status();
+    }
     if (a.drop == 0) plan_dispatch<0, EXPORT>(a, lm, ex, st);
     else if (a.drop == 1) plan_dispatch<1, EXPORT>(a, lm, ex, st);
     else plan_dispatch<2, EXPORT>(a, lm, ex, st);
@@ -734,6 +891,8 @@ sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStrea
 }
 
 int cover_intervals(int drop) { return drop == 0 ? Cover<0>::K : (drop == 1 ? Cover<1>::K : Cover<2>::K); }
+
+int query_intervals(int dim, int drop) { return dim == 3 ? kCells3 : cover_intervals(drop); }
 
 static unsigned flat_grid(uint64_t m)
 {

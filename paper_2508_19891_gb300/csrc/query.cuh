@@ -9,9 +9,11 @@ struct QueryArgs {
     int curve;
     const uint64_t* keys;        // sorted keys [n]
     const uint32_t* ids;         // ids in sorted order [n]
-    const int2* xy;              // coordinates in sorted order [n]
+    const int2* xy;              // coordinates in sorted order [n] (2-D)
+    const int4* xyz;             // coordinates in sorted order [n] (3-D: x, y, z, 0)
+    int dim;                     // 2 or 3; queries are int32[m][dim]
     uint32_t n;
-    const int32_t* q;            // [m][2]
+    const int32_t* q;            // [m][dim]
     const int32_t* delta;        // [m]
     uint64_t m;
     uint32_t* ranges;            // [m][2 * kint]: (begin, end) of up to kint intervals
@@ -49,6 +51,7 @@ struct LearnedModelView {
 
 sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStream_t st);
 int cover_intervals(int drop);   // intervals stored per query for a cover refinement
+int query_intervals(int dim, int drop);   // ... for an index of dimension dim
 sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
 // curve key of each query centre (invalid centres sort last) with the query index as value
 sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);

@@ -125,6 +125,44 @@ __device__ __forceinline__ void morton_decode(uint64_t k, uint32_t& x, uint32_t&
     y = gather_bits(k >> 1);
 }
 
+// Z curve in 3-D (Alg. 2 with a third coordinate): bit i of x, y, z goes to key bit 3i, 3i + 1,
+// 3i + 2; 21 bits per coordinate give 63-bit keys.  Magic-mask spread: each step splits the
+// bit groups of the previous one and moves them apart, until single bits sit 3 apart.
+constexpr int kOmega3 = 21;
+constexpr uint32_t kSide3 = 1u << kOmega3;
+
+__host__ __device__ __forceinline__ uint64_t spread3_bits(uint32_t v)
+{
+    uint64_t x = v & (kSide3 - 1);
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t gather3_bits(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x | (x >> 2)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x >> 4)) & 0x100F00F00F00F00Full;
+    x = (x | (x >> 8)) & 0x001F0000FF0000FFull;
+    x = (x | (x >> 16)) & 0x001F00000000FFFFull;
+    x = (x | (x >> 32)) & 0x00000000001FFFFFull;
+    return (uint32_t)x;
+}
+
+__host__ __device__ __forceinline__ uint64_t morton3_key(uint32_t x, uint32_t y, uint32_t z)
+{
+    return spread3_bits(x) | (spread3_bits(y) << 1) | (spread3_bits(z) << 2);
+}
+
+__device__ __forceinline__ bool point3_in_domain(int32_t x, int32_t y, int32_t z)
+{
+    return (uint32_t)x < kSide3 && (uint32_t)y < kSide3 && (uint32_t)z < kSide3;
+}
+
 // Hilbert curve as a finite-state machine.  The orientation of the sub-square being
 // refined is one of four symmetries of the square, generated by T (exchange x and y) and
 // R (complement both coordinates inside the sub-square); they commute, so a state is two
@@ -341,6 +379,10 @@ __device__ __forceinline__ int64_t leaf_predict(const LeafParams& lp, uint64_t k
 sfc_status launch_keys(const int2* pts, uint64_t n, int curve, uint64_t* keys, uint32_t* status,
                        cudaStream_t st);
 sfc_status launch_decode(const uint64_t* keys, uint64_t n, int curve, int2* pts, cudaStream_t st);
+// 3-D Z keys of int32[n][3] points (bad coordinates set SFC_DEV_BAD_POINT), and their inverse
+// into int4 (x, y, z, 0) records
+sfc_status launch_keys3(const int32_t* pts, uint64_t n, uint64_t* keys, uint32_t* status, cudaStream_t st);
+sfc_status launch_decode3(const uint64_t* keys, uint64_t n, int4* xyz, cudaStream_t st);
 
 // scan.cu: exclusive scan of uint32 (or a uint32 view) into uint64[n+1].
 struct ScanWorkspace {

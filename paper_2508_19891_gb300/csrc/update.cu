@@ -186,6 +186,8 @@ void release_index(sfc_index* idx, cudaStream_t st)
     idx->alive.release(st);
     idx->status.release(st);
     idx->occ.release(st);
+    idx->xyz.release(st);
+    idx->keys_in.release(st);
     release_sort_ws(idx->sort_ws, st);
     idx->scan_ws.flags.release(st);
     QueryWs& q = idx->qws;
@@ -356,7 +358,7 @@ extern "C" sfc_status sfc_update(sfc_index* idx, const int32_t* d_inserts, uint6
                                  const uint32_t* d_delete_ids, uint64_t k_del, uint32_t* h_first_new_id,
                                  void* stream)
 {
-    if (!idx || (k_ins && !d_inserts) || (k_del && !d_delete_ids)) return SFC_ERR_INVALID;
+    if (!idx || (k_ins && !d_inserts) || (k_del && !d_delete_ids) || idx->dim != 2) return SFC_ERR_INVALID;
     if (k_del > idx->n || k_ins >= 0xffffffffull) return k_del > idx->n ? SFC_ERR_NOT_FOUND : SFC_ERR_INVALID;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     idx->last_stream = st;

@@ -322,6 +322,43 @@ def paper_static(dist: str, n: int, m: int, rel_side: float, qdist: str = "unifo
                      "norm": "square"})
 
 
+SIDE3 = 1 << 21   # 3-D domain side (63-bit keys)
+
+
+def mixed3d(n: int = 10_000_000, m: int = 1_000_000, seed: int = 8, scale: float = 1.0,
+            n_clusters: int = 1000, sigma: float = 2.0 ** 11) -> Workload:
+    """3-D counterpart of the mixed workloads (the paper's d-dimensional remark, Sec. 2.1):
+    half the points uniform in [0, 2^21)^3, half from 1,000 isotropic Gaussian clusters with
+    sigma 2^11 (2^-10 of the side), queries at data points, and per-query radii from the
+    generator's density so that the expected count (4/3) pi delta^3 rho is log-uniform in
+    [1, 2000]."""
+    n = max(2, int(round(n * scale)))
+    m = max(1, int(round(m * scale)))
+    C = max(1, int(round(n_clusters * min(1.0, scale ** 0.5))))
+    rp, rq, rd = _streams(seed, 3)
+    n_u = n // 2
+    n_c = n - n_u
+    centres = rp.uniform(0, SIDE3, size=(C, 3))
+    pts = np.empty((n, 3), np.int64)
+    cl = np.full(n, -1, np.int64)
+    pts[:n_u] = rp.integers(0, SIDE3, size=(n_u, 3))
+    which = rp.integers(0, C, size=n_c)
+    pts[n_u:] = np.clip(np.rint(centres[which] + rp.normal(0.0, sigma, size=(n_c, 3))), 0, SIDE3 - 1)
+    cl[n_u:] = which
+    perm = rp.permutation(n)
+    pts, cl = pts[perm].astype(np.int32), cl[perm]
+    qi = rq.integers(0, n, size=m)
+    qs = pts[qi].copy()
+    rho = np.full(m, n_u / float(SIDE3) ** 3)
+    sel = cl[qi] >= 0
+    r2 = ((qs[sel].astype(np.float64) - centres[cl[qi][sel]]) ** 2).sum(axis=1)
+    rho[sel] += (n_c / C) / ((2 * math.pi) ** 1.5 * sigma ** 3) * np.exp(-r2 / (2 * sigma ** 2))
+    kstar = np.exp(rd.uniform(math.log(1.0), math.log(2000.0), size=m))
+    delta = np.clip(np.rint(np.cbrt(kstar / (4.0 / 3.0 * math.pi * rho))), 1, SIDE3 - 1).astype(np.int32)
+    return Workload("mixed3d-1e7", pts, qs, delta, {"seed": seed, "clusters": C, "sigma": sigma,
+                                                    "k_range": [1, 2000], "dim": 3})
+
+
 WORKLOADS = {
     "uniform-1e5": uniform_1e5,
     "mixed-1e7": mixed_1e7,
