@@ -726,12 +726,13 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 // write_kernel
 // ------------------------------------------------------------------------------------
 template <int WPL, int GEOM>
-__global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
+__global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
 {
-    // per-warp staging of the array positions of one group of 32 mask words (<= 1024 hits)
-    __shared__ uint32_t s_pos[kThreads / 32][1024];
+    // per-warp staging of one group of 32 mask words (<= 1024 hits): each hit's index within
+    // the group's 1024 points, 16 bits; its array position is resolved in the copy loop
+    __shared__ uint16_t s_rel[kThreads / 32][1024];
     __shared__ WarpTab s_tab[kThreads / 32];
-    uint32_t* buf = s_pos[threadIdx.x >> 5];
+    uint16_t* buf = s_rel[threadIdx.x >> 5];
     WarpTab* tab = &s_tab[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
@@ -749,6 +750,7 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
             if (k == 0) continue;
             const QView v = load_query(a, q, tab);
             uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
+            uint32_t shift = 0, end = 0;
             const uint64_t off = a.out_offsets[q];
             const uint64_t cb = __ldg(a.chunk_base + q);
             const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
@@ -776,29 +778,25 @@ __global__ void __launch_bounds__(kThreads) write_kernel(QueryArgs a)
                     const uint32_t incl = warp_incl_scan_u32(pc);
                     const uint32_t K = __shfl_sync(0xffffffffu, incl, 31);
                     if (K == 0) continue;
-                    // each lane lists the positions of its own word's hits
+                    // each lane lists the group-relative indices of its own word's hits
                     uint32_t slot = incl - pc;
                     uint32_t bits = wl;
-                    const uint32_t fbase = s0 + ((uint32_t)(s * 32) + lane) * 32u;
-                    if (bits) {
-                        // the lane's cursor moves to the word's interval; bits past its end
-                        // move it further
-                        uint32_t shift, end;
-                        seek(tab, v.nint, fbase, cr, shift, end);
-                        while (bits) {
-                            const uint32_t f = fbase + (uint32_t)(__ffs(bits) - 1);
-                            bits &= bits - 1;
-                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
-                            buf[slot++] = f + shift;
-                        }
+                    const uint32_t rbase = lane * 32u;
+                    while (bits) {
+                        buf[slot++] = (uint16_t)(rbase + (uint32_t)(__ffs(bits) - 1));
+                        bits &= bits - 1;
                     }
                     __syncwarp();
-                    // coalesced gather of the ids and write of the output
+                    // coalesced gather of the ids and write of the output; a lane's indices
+                    // grow with t, so its interval cursor only moves forward
+                    const uint32_t gbase = s0 + (uint32_t)s * 1024u;
                     const uint64_t dst0 = off + rank;
 #pragma unroll 4
                     for (uint32_t t = lane; t < K; t += 32) {
+                        const uint32_t f = gbase + buf[t];
+                        if (f >= end) seek(tab, v.nint, f, cr, shift, end);
                         const uint64_t dst = dst0 + t;
-                        const uint32_t id = __ldg(a.ids + buf[t]);
+                        const uint32_t id = __ldg(a.ids + (f + shift));
                         if (dst < a.ids_capacity) a.out_ids[dst] = id;
                     }
                     __syncwarp();
