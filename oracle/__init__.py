@@ -106,6 +106,8 @@ def _L():
         lib.oracle_build3.argtypes = [P, u64, c_int, P, P, P]
         lib.oracle_cells3.restype = c_int
         lib.oracle_cells3.argtypes = [i32, i32, i32, i32, c_int, P, P, P]
+        lib.oracle_cells3_refined.restype = c_int
+        lib.oracle_cells3_refined.argtypes = [i32, i32, i32, i32, c_int, c_int, P, P, c_int]
         lib.oracle_query3.restype = c_int
         lib.oracle_query3.argtypes = [P, P, P, u64, P, P, u64, c_int, P, P, P]
         lib.oracle_brute3.restype = c_int
@@ -326,6 +328,18 @@ def cells3(qx: int, qy: int, qz: int, delta: int, w: int = OMEGA3):
     if cnt < 0:
         raise AssertionError("more than eight cells")
     return [(int(lo[i]), int(hi[i])) for i in range(cnt)], int(lv.value)
+
+
+def cells3_refined(qx: int, qy: int, qz: int, delta: int, w: int = OMEGA3, drop: int = 1):
+    """Key intervals of the cells `drop` levels below cells(Q) in 3-D that contain an integer
+    point of the closed ball, sorted by lo (not merged)."""
+    maxc = (2 ** drop + 1) ** 3
+    lo = np.zeros(maxc, np.uint64)
+    hi = np.zeros(maxc, np.uint64)
+    cnt = _L().oracle_cells3_refined(int(qx), int(qy), int(qz), int(delta), int(w), int(drop), _ptr(lo), _ptr(hi), maxc)
+    if cnt < 0:
+        raise AssertionError("more cells than (2^drop + 1)^3")
+    return [(int(lo[i]), int(hi[i])) for i in range(cnt)]
 
 
 def query3(index: Index, q: np.ndarray, delta: np.ndarray):

@@ -604,3 +604,48 @@ int oracle_brute3(const int32_t* xyz, uint64_t n, const int32_t* q, const int32_
     }
     return 0;
 }
+
+/* Refined 3-D cover (as oracle_cells_refined in 2-D): the cells of level max(0, l - drop)
+ * that contain an integer point of the closed ball (the distance from q to the cell's
+ * nearest integer point is at most delta), at most (2^drop + 1)^3; sorted by lo, not merged.
+ * Returns -1 if more than maxc. */
+int oracle_cells3_refined(int32_t qx, int32_t qy, int32_t qz, int32_t delta, int w, int drop, uint64_t* lo,
+                          uint64_t* hi, int maxc)
+{
+    const int64_t side = (int64_t)1 << w;
+    const int64_t d = delta;
+    const int64_t c[3] = {qx, qy, qz};
+    int64_t a0[3], a1[3];
+    for (int k = 0; k < 3; ++k) {
+        a0[k] = c[k] - d < 0 ? 0 : c[k] - d;
+        a1[k] = c[k] + d > side - 1 ? side - 1 : c[k] + d;
+    }
+    int l = oracle_level(d, w) - drop;
+    if (l < 0) l = 0;
+    int cnt = 0;
+    for (int64_t cz = a0[2] >> l; cz <= (a1[2] >> l); ++cz)
+        for (int64_t cy = a0[1] >> l; cy <= (a1[1] >> l); ++cy)
+            for (int64_t cx = a0[0] >> l; cx <= (a1[0] >> l); ++cx) {
+                const int64_t cc[3] = {cx, cy, cz};
+                int64_t dist2 = 0;
+                for (int k = 0; k < 3; ++k) {
+                    const int64_t b0 = cc[k] << l, b1 = ((cc[k] + 1) << l) - 1;
+                    const int64_t e = c[k] < b0 ? b0 - c[k] : (c[k] > b1 ? c[k] - b1 : 0);
+                    dist2 += e * e;
+                }
+                if (dist2 > d * d) continue;
+                if (cnt == maxc) return -1;
+                const uint64_t corner = oracle_key_z3((uint32_t)(cx << l), (uint32_t)(cy << l), (uint32_t)(cz << l), w);
+                const uint64_t span = (3 * l >= 64) ? ~(uint64_t)0 : (((uint64_t)1 << (3 * l)) - 1);
+                lo[cnt] = corner & ~span;
+                hi[cnt] = lo[cnt] + span;
+                ++cnt;
+            }
+    for (int i = 1; i < cnt; ++i) {
+        const uint64_t a = lo[i], b = hi[i];
+        int j = i - 1;
+        while (j >= 0 && lo[j] > a) { lo[j + 1] = lo[j]; hi[j + 1] = hi[j]; --j; }
+        lo[j + 1] = a; hi[j + 1] = b;
+    }
+    return cnt;
+}

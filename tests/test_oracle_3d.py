@@ -90,3 +90,30 @@ def test_query3_matches_brute_force(w, maxd, n):
         seg = ids[off[i]:off[i + 1]]
         pairs = list(zip(kmap[seg], seg))
         assert pairs == sorted(pairs)
+
+
+@pytest.mark.parametrize("drop", [1, 2])
+def test_cells3_refined(drop):
+    """Finer 3-D covers: every integer point of the closed ball is covered, every kept cell
+    holds one, disjoint, at most (2^drop + 1)^3 cells of side 2^max(0, l - drop)."""
+    w = 3
+    side = 1 << w
+    g = np.stack(np.meshgrid(np.arange(side), np.arange(side), np.arange(side), indexing="ij"), -1).reshape(-1, 3)
+    keys = np.array([oracle.key_z3(*p, w) for p in g], dtype=np.int64)
+    rng = np.random.default_rng(drop)
+    for qi in rng.choice(len(g), 40, replace=False):
+        q = g[qi]
+        for d in range(0, side + 2):
+            r = oracle.cells3_refined(*q, d, w, drop)
+            l = max(0, oracle.level(d, w) - drop)
+            assert len(r) <= (2 ** drop + 1) ** 3
+            inball = ((g - q) ** 2).sum(axis=1) <= d * d
+            kb = keys[inball]
+            cov = np.zeros(kb.shape, bool)
+            for lo, hi in r:
+                assert hi - lo + 1 == 8 ** l and lo % (8 ** l) == 0
+                assert (((keys >= lo) & (keys <= hi)) & inball).any()
+                cov |= (kb >= lo) & (kb <= hi)
+            assert cov.all()
+            for (a, b), (c, e) in zip(r, r[1:]):
+                assert b < c
