@@ -204,8 +204,8 @@ def run_ours(args, rank, world, local):
         opts["occupancy_depth"] = args.occupancy
     norm = wl.meta.get("norm", "disc")
     opts["query_norm"] = norm
-    if dim == 3:
-        opts = {"profile": 1}
+    if dim == 3:   # 3-D: binary bounds, disc windows; the cover may be cells(Q) or one level finer
+        opts = {"profile": 1, "cover_refine": args.cover if args.cover is not None and args.cover < 2 else -1}
 
     # size the output once (the total is the same for every step) and let the autotuner pick
     # the cover, the scan's chunk size and work-queue batches for this shape

@@ -126,10 +126,12 @@ sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, 
  * cells(Q) has at most 2^3 = 8 cells.  The query calls (sfc_query_count / _write / _batch /
  * _batch_host, sfc_query_ranges, sfc_autotune, graphs, sfc_rebuild with int32[n][3] points)
  * take int32[m][3] centres on such an index and report the closed ball
- * dx^2 + dy^2 + dz^2 <= delta^2.  Static and with binary-search bounds only: opt->bounds must
- * be SFC_BOUNDS_BINARY, cover_refine 0 (or -1), occupancy_depth 0, query_norm SFC_NORM_DISC
- * (else SFC_ERR_INVALID); sfc_update, sfc_train_model, a learned bound search, finer covers
- * and square windows return SFC_ERR_INVALID on it; queries run in input order. */
+ * dx^2 + dy^2 + dz^2 <= delta^2.  Covers: cover_refine 0 (cells(Q)) or 1 (the cells one level
+ * finer that hold an integer point of the ball, at most 27), -1 tuned by sfc_autotune.
+ * Static and with binary-search bounds only: opt->bounds must be SFC_BOUNDS_BINARY,
+ * occupancy_depth 0, query_norm SFC_NORM_DISC, cover_refine -1..1 (else SFC_ERR_INVALID);
+ * sfc_update, sfc_train_model, a learned bound search, cover 2 and square windows return
+ * SFC_ERR_INVALID on it; queries run in input order. */
 sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt,
                       void* stream);
 

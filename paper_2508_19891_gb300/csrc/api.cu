@@ -640,6 +640,7 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
         if (idx->opt.cover_refine < 0) {   // the cover: whole batches (both passes) per candidate
             for (int d : {0, 1, 2}) {
                 if (s != SFC_OK) break;
+                if (idx->dim == 3 && d > 1) break;   // 3-D covers: cells(Q) or one level finer
                 idx->drop = d;
                 s = time_on(st, 2, &t, [&]() {
                     sfc_status c = count();
@@ -708,7 +709,7 @@ sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm)
 
 sfc_status sfc_set_cover(sfc_index* idx, int refine)
 {
-    if (!idx || refine < 0 || refine > 2 || (idx->dim == 3 && refine != 0)) return SFC_ERR_INVALID;
+    if (!idx || refine < 0 || refine > 2 || (idx->dim == 3 && refine > 1)) return SFC_ERR_INVALID;
     idx->drop = refine;
     return SFC_OK;
 }
@@ -911,11 +912,10 @@ sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, cons
     sfc_options o;
     sfc_default_options(&o);
     if (opt) o = *opt;
-    if (o.bounds != SFC_BOUNDS_BINARY || o.cover_refine > 0 || o.occupancy_depth != 0 ||
+    if (o.bounds != SFC_BOUNDS_BINARY || o.cover_refine > 1 || o.cover_refine < -1 || o.occupancy_depth != 0 ||
         o.query_norm != SFC_NORM_DISC || o.mask_budget_mb < 1 ||
         (o.chunk != 0 && (o.chunk < 32 || o.chunk > 4096 || (o.chunk & 31))))
         return SFC_ERR_INVALID;
-    o.cover_refine = 0;
     o.reorder_queries = 0;
     cudaStream_t st = as_stream(stream);
     sfc_index* idx = new (std::nothrow) sfc_index();
@@ -923,6 +923,7 @@ sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, cons
     cudaGetDevice(&idx->device);
     idx->curve = SFC_CURVE_Z;
     idx->dim = 3;
+    idx->drop = o.cover_refine < 0 ? 1 : o.cover_refine;
     idx->n = n;
     idx->opt = o;
     idx->chunk = o.chunk ? (uint32_t)o.chunk : 1024u;

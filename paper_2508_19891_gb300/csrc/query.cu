@@ -362,13 +362,21 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
 // ------------------------------------------------------------------------------------
 // plan3_kernel: the same for 3-D points (Z curve in Z^3, binary bound search)
 // ------------------------------------------------------------------------------------
-constexpr int kCells3 = 8;   // cells(Q) in 3-D: at most two per axis
+// cells(Q) in 3-D: at most two cells per axis, 8 in all; one level finer, at most 3 per axis
+template <int DROP>
+struct Cover3 {
+    static constexpr int NX = DROP == 0 ? 2 : 3;
+    static constexpr int K = NX * NX * NX;
+};
 
-// cells(Q) in 3-D: the cells of level l (2 delta <= 2^l < 4 delta, capped at 21) meeting the
-// clipped cube Q, key intervals of length 8^l, sorted, abutting ones merged.
+// DROP 0: cells(Q) in 3-D, the cells of level l (2 delta <= 2^l < 4 delta, capped at 21)
+// meeting the clipped cube Q.  DROP 1: the cells of level max(0, l - 1) holding an integer
+// point of the closed ball.  Key intervals of length 8^l, sorted, abutting ones merged.
+template <int DROP>
 __device__ __forceinline__ int derive_ranges3(int32_t qx, int32_t qy, int32_t qz, int32_t delta, uint64_t* lo,
                                               uint64_t* hi)
 {
+    constexpr int K = Cover3<DROP>::K;
     const int64_t d = delta;
     const int64_t c[3] = {qx, qy, qz};
     int64_t a0[3], a1[3];
@@ -382,12 +390,24 @@ __device__ __forceinline__ int derive_ranges3(int32_t qx, int32_t qy, int32_t qz
         l = 64 - __clzll((unsigned long long)(2 * d - 1));
         if (l > kOmega3) l = kOmega3;
     }
+    l = max(0, l - DROP);
     const uint64_t span = (1ull << (3 * l)) - 1;   // 3 l <= 63
     int cnt = 0;
     for (int64_t cz = a0[2] >> l; cz <= (a1[2] >> l); ++cz)
         for (int64_t cy = a0[1] >> l; cy <= (a1[1] >> l); ++cy)
             for (int64_t cx = a0[0] >> l; cx <= (a1[0] >> l); ++cx) {
-                if (cnt == kCells3) break;   // unreachable: at most two cells per axis
+                if (DROP > 0) {
+                    const int64_t cc[3] = {cx, cy, cz};
+                    int64_t dist2 = 0;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int64_t b0 = cc[k] << l, b1 = ((cc[k] + 1) << l) - 1;
+                        const int64_t e = c[k] < b0 ? b0 - c[k] : (c[k] > b1 ? c[k] - b1 : 0);
+                        dist2 += e * e;
+                    }
+                    if (dist2 > d * d) continue;
+                }
+                if (cnt == K) break;   // unreachable: at most Cover3<DROP>::NX cells per axis
                 const uint64_t k0 = morton3_key((uint32_t)(cx << l), (uint32_t)(cy << l), (uint32_t)(cz << l)) & ~span;
                 int j = cnt;
                 while (j > 0 && lo[j - 1] > k0) { lo[j] = lo[j - 1]; hi[j] = hi[j - 1]; --j; }
@@ -408,9 +428,11 @@ __device__ __forceinline__ int derive_ranges3(int32_t qx, int32_t qy, int32_t qz
     return m;
 }
 
-template <bool EXPORT>
+template <int DROP, bool EXPORT>
 __global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExport ex)
 {
+    constexpr int kCells3 = Cover3<DROP>::K;
+    constexpr int NB = (2 * kCells3 + 7) / 8;
     const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = i < a.m;
     int32_t qx = 0, qy = 0, qz = 0, delta = -1;
@@ -424,11 +446,11 @@ __global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExp
     if (active && !ok) set_status(a.status, SFC_DEV_BAD_QUERY);
     uint64_t lo[kCells3], hi[kCells3];
     uint32_t b[kCells3], e[kCells3];
-    const int cnt = ok ? derive_ranges3(qx, qy, qz, delta, lo, hi) : 0;
+    const int cnt = ok ? derive_ranges3<DROP>(qx, qy, qz, delta, lo, hi) : 0;
     BoundStats bs;
     const BinaryBounds bounds{};
 #pragma unroll 1
-    for (int bi = 0; bi < 2 && 8 * bi < 2 * cnt; ++bi) {
+    for (int bi = 0; bi < NB && 8 * bi < 2 * cnt; ++bi) {
         uint64_t t[8];
         uint32_t r[8];
 #pragma unroll
@@ -477,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExp
 // ------------------------------------------------------------------------------------
 // Shared helpers of the two scan passes
 // ------------------------------------------------------------------------------------
-constexpr int kMaxInt = 25;   // intervals per query at the finest cover
+constexpr int kMaxInt = 27;   // intervals per query at the finest cover (3-D, one level finer)
 
 // One query's intervals in the concatenated order of its scan (per-warp shared memory):
 // array position = concatenated index + shift[r] for indices below end[r].
@@ -872,7 +894,9 @@ static sfc_status plan_launch(const QueryArgs& a, const LearnedModelView* lm, co
 {
     if (a.m == 0) return SFC_OK;
     if (a.dim == 3) {
-        plan3_kernel<EXPORT><<<(unsigned)((a.m + kThreads - 1) / kThreads), kThreads, 0, st>>>(a, ex);
+        const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
+        if (a.drop == 0) plan3_kernel<0, EXPORT><<<g, kThreads, 0, st>>>(a, ex);
+        else plan3_kernel<1, EXPORT><<<g, kThreads, 0, st>>>(a, ex);
         count_launch();
         return launch_status();
     }
@@ -890,7 +914,11 @@ sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStrea
 
 int cover_intervals(int drop) { return drop == 0 ? Cover<0>::K : (drop == 1 ? Cover<1>::K : Cover<2>::K); }
 
-int query_intervals(int dim, int drop) { return dim == 3 ? kCells3 : cover_intervals(drop); }
+int query_intervals(int dim, int drop)
+{
+    if (dim == 3) return drop == 0 ? Cover3<0>::K : Cover3<1>::K;
+    return cover_intervals(drop);
+}
 
 static unsigned flat_grid(uint64_t m)
 {

@@ -43,7 +43,8 @@ def test_build3_sorted_arrays(cuda, n):
     assert np.array_equal(xs[:, :3], ref.xy) and not xs[:, 3].any()
 
 
-def test_ranges3(cuda):
+@pytest.mark.parametrize("cover", [0, 1])
+def test_ranges3(cuda, cover):
     rng = np.random.default_rng(5)
     p = _pts(rng, 20_000)
     qs = np.concatenate([p[:1500], _pts(rng, 500)])
@@ -51,19 +52,23 @@ def test_ranges3(cuda):
     d[:20] = 0
     d[20:30] = S3
     qs[30:34] = [[0, 0, 0], [S3 - 1, S3 - 1, S3 - 1], [0, S3 - 1, 5], [7, 7, S3 - 1]]
-    idx = sfc.sfc_build3(to_dev(p, cuda))
-    assert sfc.sfc_query_max_intervals(idx) == 8
+    idx = sfc.sfc_build3(to_dev(p, cuda), cover_refine=cover)
+    K = sfc.sfc_query_max_intervals(idx)
+    assert K == (8 if cover == 0 else 27)
     lo, hi, b, e, c = sfc.sfc_query_ranges(idx, to_dev(qs, cuda), to_dev(d, cuda))
     lo, hi, b, e, c = u64(lo), u64(hi), b.cpu().numpy(), e.cpu().numpy(), c.cpu().numpy()
     ref = oracle.build3(p)
     for j in range(len(qs)):
-        cells, _ = oracle.cells3(*qs[j], int(d[j]))
+        if cover == 0:
+            cells, _ = oracle.cells3(*qs[j], int(d[j]))
+        else:
+            cells = oracle.cells3_refined(*qs[j], int(d[j]), drop=1)
         merged = oracle.merge_abutting(cells)
-        assert c[j] == len(merged) <= 8
+        assert c[j] == len(merged) <= K
         for r, (a, z) in enumerate(merged):
-            assert (int(lo[8 * j + r]), int(hi[8 * j + r])) == (a, z)
-            assert b[8 * j + r] == oracle.lower_bound(ref.keys, a)
-            assert e[8 * j + r] == oracle.lower_bound(ref.keys, z + 1)
+            assert (int(lo[K * j + r]), int(hi[K * j + r])) == (a, z)
+            assert b[K * j + r] == oracle.lower_bound(ref.keys, a)
+            assert e[K * j + r] == oracle.lower_bound(ref.keys, z + 1)
 
 
 def _same(idx, p, qs, d, cuda):
@@ -75,9 +80,10 @@ def _same(idx, p, qs, d, cuda):
 
 
 @pytest.mark.parametrize("chunk", [32, 1024, 4096])
-def test_mixed3d_vs_oracle(cuda, chunk):
+@pytest.mark.parametrize("cover", [0, 1])
+def test_mixed3d_vs_oracle(cuda, chunk, cover):
     wl = W.mixed3d(scale=0.005)
-    idx = sfc.sfc_build3(to_dev(wl.points, cuda), chunk=chunk)
+    idx = sfc.sfc_build3(to_dev(wl.points, cuda), chunk=chunk, cover_refine=cover)
     _same(idx, wl.points, wl.queries, wl.delta, cuda)
     assert sfc.sfc_device_status(idx) == (0, 0)
 
@@ -91,7 +97,7 @@ def test_dense_small_grid_edge_cases(cuda):
     qs = np.concatenate([p[rng.integers(0, len(p), 3000)], np.array([[3, 4, 5], [0, 0, 0], [-1, 0, 0], [0, S3, 0]], np.int32)])
     d = np.concatenate([rng.integers(0, 12, 3000), np.array([0, 2 ** 31 - 1, 5, 5])]).astype(np.int32)
     d[7] = -2
-    idx = sfc.sfc_build3(to_dev(p, cuda), mask_budget_mb=1)
+    idx = sfc.sfc_build3(to_dev(p, cuda), mask_budget_mb=1, cover_refine=1)
     off, _ = _same(idx, p, qs, d, cuda)
     o = u64(off)
     assert o[3001] - o[3000] >= 300 and o[3002] - o[3001] == len(p)
@@ -108,7 +114,10 @@ def test_host_rebuild_graph_autotune(cuda):
     assert np.array_equal(off, roff) and np.array_equal(ids, rids)
     pts, q, d = to_dev(wl.points, cuda), to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
     tuned = sfc.sfc_autotune(idx, q, d, force=True)
-    assert tuned["cover"] == 0
+    assert tuned["cover"] == 0   # built with the default cover_refine = 0: not tuned
+    idx_t = sfc.sfc_build3(pts, cover_refine=-1)
+    assert sfc.sfc_autotune(idx_t, q, d, force=True)["cover"] in (0, 1)
+    _same(idx_t, wl.points, wl.queries, wl.delta, cuda)
     roff2, rids2 = oracle.query3(oracle.build3(wl2.points), wl.queries, wl.delta)
     total = max(int(roff[-1]), int(roff2[-1]))
     o = torch.zeros(wl.m + 1, dtype=torch.int64, device=cuda)
@@ -128,7 +137,7 @@ def test_host_rebuild_graph_autotune(cuda):
 
 def test_rejections(cuda):
     p = to_dev(_pts(np.random.default_rng(2), 1000), cuda)
-    for bad in ({"bounds": "learned"}, {"cover_refine": 1}, {"occupancy_depth": 4}, {"query_norm": "square"}):
+    for bad in ({"bounds": "learned"}, {"cover_refine": 2}, {"occupancy_depth": 4}, {"query_norm": "square"}):
         with pytest.raises(sfc.SfcError):
             sfc.sfc_build3(p, **bad)
     idx = sfc.sfc_build3(p)
@@ -137,7 +146,8 @@ def test_rejections(cuda):
     with pytest.raises(sfc.SfcError):
         sfc.sfc_train_model(idx)
     with pytest.raises(sfc.SfcError):
-        sfc.sfc_set_cover(idx, 1)
+        sfc.sfc_set_cover(idx, 2)
+    sfc.sfc_set_cover(idx, 1)
     with pytest.raises(sfc.SfcError):
         sfc.sfc_set_query_norm(idx, "square")
     bad = to_dev(np.array([[0, 0, S3]], np.int32), cuda)
