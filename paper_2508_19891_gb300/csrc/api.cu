@@ -255,6 +255,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         dst.vals = w.perm.as<uint32_t>();
         dst.curve = idx->curve;
         SFC_TRY(radix_sort(src, m, dst, idx->sort_ws, a.status, st));
+        a.perm = w.perm.as<uint32_t>();   // the plan already runs in processing order
     }
     {
         ProfScope ps(idx, "plan", st);
@@ -267,7 +268,6 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
             SFC_TRY(launch_gather_u32(a.nchunks, w.perm.as<uint32_t>(), m, w.nch_sorted.as<uint32_t>(), st));
             SFC_TRY(exclusive_scan_u32(w.nch_sorted.as<uint32_t>(), m, w.wbase.as<uint64_t>(), idx->scan_ws,
                                        a.status, st));
-            a.perm = w.perm.as<uint32_t>();
             a.wbase = w.wbase.as<uint64_t>();
         }
     }

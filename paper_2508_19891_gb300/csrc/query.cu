@@ -297,8 +297,11 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
     bounds.prepare(&s_root);
     __syncthreads();
     if (a.curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);   // ends with a block barrier
-    const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
-    const bool active = i < a.m;
+    // thread r takes the query of processing rank r (curve order of the centres when a
+    // processing order is given: neighbouring threads then search neighbouring keys)
+    const uint64_t r = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = r < a.m;
+    const uint64_t i = active && a.perm ? (uint64_t)__ldg(a.perm + r) : r;
     int2 q = make_int2(0, 0);
     int32_t delta = -1;
     if (active) {
@@ -819,7 +822,7 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
                         if (f >= end) seek(tab, v.nint, f, cr, shift, end);
                         const uint64_t dst = dst0 + t;
                         const uint32_t id = __ldg(a.ids + (f + shift));
-                        if (dst < a.ids_capacity) a.out_ids[dst] = id;
+                        if (dst < a.ids_capacity) __stcs(a.out_ids + dst, id);   // written once, not re-read
                     }
                     __syncwarp();
                     rank += K;
@@ -835,7 +838,9 @@ __global__ void query_keys_kernel(const int32_t* __restrict__ q, uint64_t m, int
     if (curve == SFC_CURVE_HILBERT) hilbert_tables_init(&tb);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
         const int2 c = reinterpret_cast<const int2*>(q)[i];
-        keys[i] = point_in_domain(c.x, c.y) ? curve_key(curve, &tb, (uint32_t)c.x, (uint32_t)c.y) : ~0ull;
+        // the top 32 of the 60 key bits (cells of side 2^14) order the queries well enough, and
+        // the sort skips the four constant low digits
+        keys[i] = point_in_domain(c.x, c.y) ? curve_key(curve, &tb, (uint32_t)c.x, (uint32_t)c.y) >> 28 : ~0ull >> 28;
     }
 }
 
