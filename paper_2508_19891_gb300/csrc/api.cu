@@ -200,6 +200,7 @@ const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
     if (idx->bounds != SFC_BOUNDS_LEARNED || !idx->model.trained) return nullptr;
     v.root = model_root_device(idx);
     v.leaf = idx->model.leaves.as<LeafParams>();
+    v.fence = idx->model.fence.as<uint64_t>();
     v.stats = model_stats(idx);
     return &v;
 }

@@ -38,6 +38,7 @@ struct ModelState {
     DevBuf partial;    // per-block partial gradients and the completion counter
     DevBuf tmp;        // per-leaf first/last position and error extremes during a fit
     DevBuf leaves;     // LeafParams[nleaves], read by the query path
+    DevBuf fence;      // uint64[nleaves][kFence]: fence keys of each leaf, read by the query path
     DevBuf route;      // leaf of every key (uint32[n])
 };
 

@@ -659,6 +659,18 @@ __global__ void leaf_store_err_kernel(const LeafTmp* tmp, LeafParams* leaf, int 
     }
 }
 
+// The fence of every leaf (kFence keys at equally spaced positions of its range); a leaf with
+// no keys gets keys that no target exceeds.
+__global__ void fence_kernel(const uint64_t* __restrict__ keys, const LeafParams* __restrict__ leaf, int leaves,
+                             uint64_t* __restrict__ fence)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= leaves * kFence) return;
+    const int j = i / kFence, s = i - j * kFence;
+    const uint64_t first = leaf[j].first, c = leaf[j].end - leaf[j].first;
+    fence[i] = c ? keys[first + ((uint64_t)s * c) / kFence] : ~0ull;
+}
+
 }  // namespace
 
 const RootParams* model_root_device(sfc_index* idx)
@@ -696,6 +708,9 @@ sfc_status fit_leaves(sfc_index* idx, cudaStream_t st)
     }
     leaf_store_err_kernel<<<(leaves + 255) / 256, 256, 0, st>>>(tmp, lp, leaves);
     count_launch();
+    SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
+    fence_kernel<<<(leaves * kFence + 255) / 256, 256, 0, st>>>(keys, lp, leaves, M.fence.as<uint64_t>());
+    count_launch();
     return launch_status();
 }
 
@@ -714,6 +729,7 @@ sfc_status reserve_model(sfc_index* idx, uint64_t n, cudaStream_t st)
     SFC_TRY(M.partial.ensure((size_t)kTrainBlocks * kPartial * sizeof(long long) + 256, st));
     SFC_TRY(M.tmp.ensure((size_t)leaves * sizeof(LeafTmp), st));
     SFC_TRY(M.leaves.ensure((size_t)leaves * sizeof(LeafParams), st));
+    SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
     SFC_TRY(M.route.ensure(std::max<uint64_t>(n, 1) * sizeof(uint32_t), st));
     return SFC_OK;
 }

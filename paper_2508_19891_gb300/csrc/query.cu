@@ -72,6 +72,7 @@ struct BoundStats {
 // Bound search functors: lower_bound of t[0..ne) (ne <= E) into r[].
 struct BinaryBounds {
     static constexpr bool kStats = false;
+    static constexpr int kBatch = 8;   // endpoints searched in lock step per thread
     __device__ __forceinline__ void prepare(RootParams*) {}
     template <int E>
     __device__ __forceinline__ void search(const uint64_t* keys, uint32_t n, const uint64_t* t, uint32_t* r,
@@ -88,8 +89,10 @@ struct BinaryBounds {
 
 struct LearnedBounds {
     static constexpr bool kStats = true;
+    static constexpr int kBatch = 4;
     const RootParams* root;      // device; after prepare() the block's shared-memory copy
     const LeafParams* leaf;
+    const uint64_t* fence;       // [leaves][kFence] fence keys
     unsigned long long* stats;   // [0] endpoints, [1] misses, [2] window sum
     // every thread of the block calls this, then the block synchronises
     __device__ __forceinline__ void prepare(RootParams* s)
@@ -104,11 +107,17 @@ struct LearnedBounds {
                                            int ne, BoundStats& bs) const
     {
         uint32_t lo[E], len[E];
+        int jl[E];
+        uint32_t fl[E], fn[E];   // fence search: the number of fence keys below t lies in [fl, fl + fn]
         unsigned long long wsum = 0;
+        // the leaf of each target and its window: prediction + stored error extremes
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             lo[e] = 0;
             len[e] = 0;
+            jl[e] = 0;
+            fl[e] = 0;
+            fn[e] = 0;
             if (e < ne) {
                 const int j = route_leaf(*root, t[e]);
                 const LeafParams lp = leaf[j];
@@ -120,6 +129,45 @@ struct LearnedBounds {
                 b = min(b, (int64_t)lp.end);
                 lo[e] = (uint32_t)a;
                 len[e] = (uint32_t)(b - a);
+                jl[e] = j;
+                fn[e] = lp.end > lp.first ? kFence : 0;
+            }
+        }
+        // bracket each target between two fence keys of its leaf (one 128-byte line per leaf)
+        while (true) {
+            bool any = false;
+#pragma unroll
+            for (int e = 0; e < E; ++e) any |= fn[e] > 0;
+            if (!any) break;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (fn[e] > 0) {
+                    const uint32_t half = fn[e] >> 1;
+                    const bool right = __ldg(fence + (size_t)jl[e] * kFence + fl[e] + half) < t[e];
+                    fl[e] = right ? fl[e] + half + 1 : fl[e];
+                    fn[e] = right ? fn[e] - half - 1 : half;
+                }
+            }
+        }
+        // s fence keys below t: lower_bound(t) lies between the positions of fence keys s - 1 and
+        // s; the search takes the intersection with the model's window
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (e < ne) {
+                const uint64_t first = __ldg(&leaf[jl[e]].first), c = __ldg(&leaf[jl[e]].end) - first;
+                if (c) {
+                    const uint64_t sfn = fl[e];
+                    const uint64_t bl = sfn == 0 ? first : first + ((sfn - 1) * c) / kFence + 1;
+                    const uint64_t bh = sfn == kFence ? first + c : first + (sfn * c) / kFence;
+                    const uint64_t nl = max((uint64_t)lo[e], bl), nh = min((uint64_t)lo[e] + len[e], bh);
+                    if (nl <= nh) {
+                        lo[e] = (uint32_t)nl;
+                        len[e] = (uint32_t)(nh - nl);
+                    } else {
+                        lo[e] = (uint32_t)bl;
+                        len[e] = (uint32_t)(bh - bl);
+                    }
+                }
                 wsum += len[e];
             }
         }
@@ -248,25 +296,26 @@ __device__ __forceinline__ int query_bounds(const Bounds& bounds, const QueryArg
                                             uint32_t& nempty)
 {
     constexpr int K = Cover<DROP>::K;
-    constexpr int NB = (2 * K + 7) / 8;
+    constexpr int BW = Bounds::kBatch;
+    constexpr int NB = (2 * K + BW - 1) / BW;
     const uint64_t* keys = a.keys;
     const uint32_t n = a.n;
     const int cnt = derive_ranges<DROP>(a.curve, a.norm, tb, qx, qy, delta, a.occ, a.occ_depth, lo, hi, ncell,
                                         nempty);
     const int ne = 2 * cnt;
 #pragma unroll 1
-    for (int bi = 0; bi < NB && 8 * bi < ne; ++bi) {
-        uint64_t t[8];
-        uint32_t r[8];
+    for (int bi = 0; bi < NB && BW * bi < ne; ++bi) {
+        uint64_t t[BW];
+        uint32_t r[BW];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const int ep = 8 * bi + x;
+        for (int x = 0; x < BW; ++x) {
+            const int ep = BW * bi + x;
             t[x] = ep < ne ? ((ep & 1) ? hi[ep >> 1] + 1 : lo[ep >> 1]) : 0;
         }
-        bounds.template search<8>(keys, n, t, r, min(max(ne - 8 * bi, 0), 8), bs);
+        bounds.template search<BW>(keys, n, t, r, min(max(ne - BW * bi, 0), BW), bs);
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const int ep = 8 * bi + x;
+        for (int x = 0; x < BW; ++x) {
+            const int ep = BW * bi + x;
             if (ep < ne) {
                 if (ep & 1) e[ep >> 1] = r[x];
                 else b[ep >> 1] = r[x];
@@ -889,7 +938,7 @@ static void plan_dispatch(const QueryArgs& a, const LearnedModelView* lm, const 
     const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
     if (lm)
         plan_kernel<LearnedBounds, DROP, EXPORT>
-            <<<g, kThreads, 0, st>>>(a, LearnedBounds{lm->root, lm->leaf, lm->stats}, ex);
+            <<<g, kThreads, 0, st>>>(a, LearnedBounds{lm->root, lm->leaf, lm->fence, lm->stats}, ex);
     else
         plan_kernel<BinaryBounds, DROP, EXPORT><<<g, kThreads, 0, st>>>(a, BinaryBounds{}, ex);
 }

@@ -46,6 +46,7 @@ struct QueryArgs {
 struct LearnedModelView {
     const RootParams* root;      // device memory (written by training, no host copy needed)
     const LeafParams* leaf;
+    const uint64_t* fence;       // [leaves][kFence] fence keys
     unsigned long long* stats;   // [3]: endpoints, misses, window sum
 };
 

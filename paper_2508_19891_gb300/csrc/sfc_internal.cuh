@@ -311,6 +311,11 @@ constexpr int kKnots = 256;
 constexpr int kRootPwl = 0;
 constexpr int kRootMlp = 1;
 
+// Each leaf also keeps a fence: the keys at kFence equally spaced positions of its range
+// (position first + s * (end - first) / kFence, s = 0 .. kFence - 1), one 128-byte line, so
+// a search first brackets its target between two fence keys.
+constexpr int kFence = 16;
+
 struct LeafParams {          // 32 bytes, one sector
     uint64_t base;           // smallest key routed to the leaf
     uint32_t first;          // first position routed to the leaf

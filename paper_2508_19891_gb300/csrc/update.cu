@@ -199,7 +199,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
     ModelState& M = idx->model;
     M.state.release(st); M.samples.release(st); M.partial.release(st);
-    M.tmp.release(st); M.leaves.release(st); M.route.release(st);
+    M.tmp.release(st); M.leaves.release(st); M.route.release(st); M.fence.release(st);
     UpdateWs& u = idx->uws;
     u.a.release(st); u.b.release(st); u.c.release(st); u.d.release(st);
     u.e.release(st); u.f.release(st); u.g.release(st); u.h.release(st);
