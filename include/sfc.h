@@ -306,6 +306,13 @@ sfc_status sfc_model_get(const sfc_index* idx, int* h_root, float* h_params, int
                          uint32_t* h_first, uint32_t* h_end, float* h_slope, float* h_icpt,
                          int32_t* h_err_lo, int32_t* h_err_hi, void* stream);
 
+/* Copies the leaves' fences out (host): uint64[*h_leaves][16], fence s of leaf j = the key at
+ * position first_j + floor(s * (end_j - first_j) / 16) of the sorted array (all bits set for a
+ * leaf without keys).  A learned search brackets its target between two fence keys before
+ * the last-mile search.  h_fence must hold leaves * 16 entries.  SFC_ERR_STATE if no model.
+ * Synchronises. */
+sfc_status sfc_model_fence(const sfc_index* idx, uint64_t* h_fence, int* h_leaves, void* stream);
+
 /* Work of the last query batch: points scanned (sum over queries of the interval lengths,
  * the S_q of Alg. 1's scan loop), scan chunks, and points reported.  Synchronises. */
 sfc_status sfc_query_stats(const sfc_index* idx, uint64_t* h_scanned, uint64_t* h_chunks,

@@ -18,6 +18,9 @@ those of ``lower_bound`` by construction.  What needs a reference is the model i
   of position against key offset; a per-leaf error window is the min and max of
   (position - predicted position) over the leaf's keys.
 
+Each leaf also keeps a fence (``leaf_fence``): the keys at 16 equally spaced positions of its
+range; ``fence_bracket`` gives the positions between which lower_bound of a target lies.
+
 Nothing here is fitted to the GPU's fp32 numbers: the gradient is the analytic derivative of
 L, pinned by central finite differences in tests/test_oracle_learned.py, and the leaf fit is
 the closed-form normal equations, pinned against numpy.polyfit.
@@ -177,3 +180,26 @@ def error_window(positions: np.ndarray, predicted: np.ndarray):
     true position of every key of the leaf."""
     d = np.asarray(positions, np.int64) - np.asarray(predicted, np.int64)
     return int(d.min()), int(d.max())
+
+
+FENCE = 16  # fence keys per leaf
+
+
+def leaf_fence(keys: np.ndarray, first: int, end: int, k: int = FENCE) -> np.ndarray:
+    """The fence of a leaf covering sorted positions [first, end): the keys at positions
+    first + floor(s * (end - first) / k), s = 0 .. k-1 (all bits set for an empty leaf)."""
+    c = int(end) - int(first)
+    if c <= 0:
+        return np.full(k, np.iinfo(np.uint64).max, np.uint64)
+    pos = int(first) + (np.arange(k, dtype=np.int64) * c) // k
+    return np.asarray(keys, np.uint64)[pos]
+
+
+def fence_bracket(fence: np.ndarray, first: int, end: int, t: int, k: int = FENCE):
+    """[lo, hi] that holds lower_bound(t) over the leaf's keys when that lies in [first, end]:
+    with s fence keys below t, between the positions of fence keys s - 1 (exclusive) and s."""
+    c = int(end) - int(first)
+    s = int(np.count_nonzero(np.asarray(fence, np.uint64) < np.uint64(t)))
+    lo = first if s == 0 else first + ((s - 1) * c) // k + 1
+    hi = end if s == k else first + (s * c) // k
+    return lo, hi

@@ -88,6 +88,7 @@ def lib():
             "sfc_reserve_queries": (ci, [P, u64, P]),
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_set_cover": (ci, [P, ci]),
+            "sfc_model_fence": (ci, [P, P, P, P]),
             "sfc_build3": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
             "sfc_build3_host": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
             "sfc_index_dim": (ci, [P]),
@@ -520,6 +521,15 @@ def sfc_model_get(index: Index, stream=None) -> dict:
                                _hptr(out["first"]), _hptr(out["end"]), _hptr(out["slope"]),
                                _hptr(out["icpt"]), _hptr(out["err_lo"]), _hptr(out["err_hi"]),
                                _stream(stream)), "sfc_model_get")
+    return out
+
+
+def sfc_model_fence(index: Index, stream=None) -> np.ndarray:
+    """uint64[leaves, 16]: the fence keys of every leaf."""
+    nl = ctypes.c_int(0)
+    _check(lib().sfc_model_fence(index.handle, None, ctypes.byref(nl), _stream(stream)), "sfc_model_fence")
+    out = np.zeros((nl.value, 16), np.uint64)
+    _check(lib().sfc_model_fence(index.handle, _hptr(out), ctypes.byref(nl), _stream(stream)), "sfc_model_fence")
     return out
 
 

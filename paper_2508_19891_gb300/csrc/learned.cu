@@ -908,4 +908,19 @@ sfc_status sfc_model_get(const sfc_index* cidx, int* h_root, float* h_params, in
     return SFC_OK;
 }
 
+sfc_status sfc_model_fence(const sfc_index* cidx, uint64_t* h_fence, int* h_leaves, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx) return SFC_ERR_INVALID;
+    if (!idx->model.trained || !idx->model.fence.ptr) return SFC_ERR_STATE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int L = idx->model.nleaves;
+    if (h_leaves) *h_leaves = L;
+    if (h_fence)
+        SFC_CUDA_TRY(cudaMemcpyAsync(h_fence, idx->model.fence.ptr, (size_t)L * kFence * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    return SFC_OK;
+}
+
 }  // extern "C"

@@ -173,3 +173,23 @@ def test_trained_vs_untrained_root(cuda):
     assert res[("pwl", 300)][1] < res[("pwl", 0)][1], res
     for v in res.values():
         assert v[0] < wl.n / 100
+
+
+@pytest.mark.parametrize("curve", ["z", "h"])
+def test_fence_matches_oracle(cuda, curve):
+    """The leaves' fences are the keys at the positions the definition gives (oracle
+    learned.leaf_fence over the oracle's sorted keys and the GPU's leaf ranges), and a learned
+    query batch still equals binary search."""
+    from oracle import learned as L
+    wl = W.mixed_1e7(scale=0.02)
+    idx = sfc.sfc_build(to_dev(wl.points, cuda), curve, bounds="learned")
+    m = sfc.sfc_model_get(idx)
+    fence = sfc.sfc_model_fence(idx)
+    ref = oracle.build(wl.points, 30, curve)
+    for j in range(len(m["first"])):
+        assert np.array_equal(fence[j], L.leaf_fence(ref.keys, int(m["first"][j]), int(m["end"][j]))), j
+    off, ids = sfc.query(idx, to_dev(wl.queries, cuda), to_dev(wl.delta, cuda))
+    roff, rids = oracle.query(ref, wl.queries, wl.delta)
+    assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+    st = sfc.sfc_model_stats(idx)
+    assert st["misses"] == 0 and st["window_sum"] / st["endpoints"] < 0.5 * wl.n / 4096 + 2

@@ -110,3 +110,23 @@ def test_pwl_least_squares_optimum_is_the_cdf_on_a_line():
     h = 0.3 + 0.5 * np.arange(K + 1) / K
     loss, g = L.pwl_loss_grad(h, x, y, K)
     assert loss < 1e-28 and np.abs(g).max() < 1e-14
+
+
+def test_fence_bracket_holds_lower_bound():
+    """The fence bracket of a leaf (Sec. 2.1's lower_bound, bounded by keys of the array at
+    equally spaced positions) always holds the true lower_bound, on duplicates too."""
+    from oracle import learned as L
+    rng = np.random.default_rng(17)
+    keys = np.sort(rng.integers(0, 1 << 40, 5000).astype(np.uint64))
+    keys[100:400] = keys[100]                          # a run of duplicates
+    for first, end in [(0, 5000), (10, 11), (37, 1237), (100, 420), (4990, 5000)]:
+        f = L.leaf_fence(keys, first, end)
+        assert np.all(np.diff(f.astype(np.float64)) >= 0)
+        for t in list(keys[first:end:7]) + list(rng.integers(int(keys[first]), int(keys[end - 1]) + 1, 300)):
+            lb = int(np.searchsorted(keys, np.uint64(t), side="left"))
+            lo, hi = L.fence_bracket(f, first, end, int(t))
+            if first <= lb <= end:
+                assert lo <= lb <= hi, (first, end, t, lb, lo, hi)
+            assert hi - lo <= (end - first) // L.FENCE + 1
+    e = L.leaf_fence(keys, 5, 5)
+    assert np.all(e == np.iinfo(np.uint64).max)
