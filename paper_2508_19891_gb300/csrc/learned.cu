@@ -516,19 +516,29 @@ __global__ void __launch_bounds__(256) route_kernel(const uint64_t* __restrict__
     __syncthreads();
     const unsigned lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // loop bound uniform per warp so the shuffles below see the whole warp
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const uint64_t i = base + threadIdx.x;
-        const bool ok = i < n;
-        const int j = ok ? route_leaf(s_root, keys[i]) : -1;
-        int prev = __shfl_up_sync(0xffffffffu, j, 1);
-        if (lane == 0 && ok && i > 0) prev = route_leaf(s_root, keys[i - 1]);
-        int next = __shfl_down_sync(0xffffffffu, j, 1);
-        if ((lane == 31 || i + 1 >= n) && ok) next = (i + 1 < n) ? route_leaf(s_root, keys[i + 1]) : -1;
-        if (ok) {
-            route[i] = (uint32_t)j;
-            if (i == 0 || prev != j) atomicMin(&tmp[j].first, (uint32_t)i);
-            if (i + 1 == n || next != j) atomicMax(&tmp[j].last, (uint32_t)i);
+    // four groups of the grid stride per iteration, their loads issued together (the loop
+    // bound is uniform per warp so the shuffles below see the whole warp)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
+        uint64_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * stride + threadIdx.x;
+            k[u] = i < n ? __ldg(keys + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * stride + threadIdx.x;
+            const bool ok = i < n;
+            const int j = ok ? route_leaf(s_root, k[u]) : -1;
+            int prev = __shfl_up_sync(0xffffffffu, j, 1);
+            if (lane == 0 && ok && i > 0) prev = route_leaf(s_root, keys[i - 1]);
+            int next = __shfl_down_sync(0xffffffffu, j, 1);
+            if ((lane == 31 || i + 1 >= n) && ok) next = (i + 1 < n) ? route_leaf(s_root, keys[i + 1]) : -1;
+            if (ok) {
+                route[i] = (uint32_t)j;
+                if (i == 0 || prev != j) atomicMin(&tmp[j].first, (uint32_t)i);
+                if (i + 1 == n || next != j) atomicMax(&tmp[j].last, (uint32_t)i);
+            }
         }
     }
 }
@@ -589,15 +599,37 @@ __global__ void __launch_bounds__(256) leaf_fit_kernel(const uint64_t* __restric
         if (threadIdx.x == 0) { leaf[blockIdx.x].slope = 0.0f; leaf[blockIdx.x].icpt = 0.0f; }
         return;
     }
+    // two passes (the mean first, for fp32 accuracy); each thread keeps four loads in flight
+    const uint64_t* kp = keys + lp.first;
+    const uint32_t B = blockDim.x;
     float su = 0.0f;
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) su += __ull2float_rn(keys[lp.first + i] - lp.base);
+    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
+        float u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = i0 + q * B;
+            u[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) : 0.0f;
+        }
+        su += (u[0] + u[1]) + (u[2] + u[3]);
+    }
     const float mu = block_sum_f(su, sh) / (float)cnt;
     const float mv = 0.5f * (float)(cnt - 1);   // mean of 0 .. cnt - 1
     float sxy = 0.0f, sxx = 0.0f;
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const float du = __ull2float_rn(keys[lp.first + i] - lp.base) - mu;
-        sxy = fmaf(du, (float)i - mv, sxy);
-        sxx = fmaf(du, du, sxx);
+    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
+        float du[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = i0 + q * B;
+            du[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) - mu : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = i0 + q * B;
+            if (i < cnt) {
+                sxy = fmaf(du[q], (float)i - mv, sxy);
+                sxx = fmaf(du[q], du[q], sxx);
+            }
+        }
     }
     sxy = block_sum_f(sxy, sh);
     sxx = block_sum_f(sxx, sh);
@@ -614,34 +646,46 @@ __global__ void __launch_bounds__(256) leaf_err_kernel(const uint64_t* __restric
 {
     const unsigned lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const uint64_t i = base + threadIdx.x;
-        const bool ok = i < n;
-        int j = -1;
-        long long e = 0;
-        if (ok) {
-            j = (int)route[i];
-            const LeafParams lp = leaf[j];
-            e = (long long)i - leaf_predict(lp, keys[i]);
-            e = e > 0x7fffffffll ? 0x7fffffffll : (e < -0x7fffffffll ? -0x7fffffffll : e);
-        }
-        // warp-aggregated when the whole warp is in one leaf (the common case)
-        const int j0 = __shfl_sync(0xffffffffu, j, 0);
-        const bool same = __all_sync(0xffffffffu, j == j0);
-        if (same) {
-            int lo = (int)e, hi = (int)e;
+    // four groups of the grid stride per iteration, their loads issued together
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
+        uint64_t k[4];
+        uint32_t jr[4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * stride + threadIdx.x;
+            k[u] = i < n ? __ldg(keys + i) : 0;
+            jr[u] = i < n ? __ldg(route + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * stride + threadIdx.x;
+            const bool ok = i < n;
+            int j = -1;
+            long long e = 0;
+            if (ok) {
+                j = (int)jr[u];
+                const LeafParams lp = leaf[j];
+                e = (long long)i - leaf_predict(lp, k[u]);
+                e = e > 0x7fffffffll ? 0x7fffffffll : (e < -0x7fffffffll ? -0x7fffffffll : e);
             }
-            if (lane == 0 && j0 >= 0) {
-                atomicMin(&tmp[j0].err_lo, lo);
-                atomicMax(&tmp[j0].err_hi, hi);
+            // warp-aggregated when the whole warp is in one leaf (the common case)
+            const int j0 = __shfl_sync(0xffffffffu, j, 0);
+            const bool same = __all_sync(0xffffffffu, j == j0);
+            if (same) {
+                int lo = (int)e, hi = (int)e;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if (lane == 0 && j0 >= 0) {
+                    atomicMin(&tmp[j0].err_lo, lo);
+                    atomicMax(&tmp[j0].err_hi, hi);
+                }
+            } else if (ok) {
+                atomicMin(&tmp[j].err_lo, (int)e);
+                atomicMax(&tmp[j].err_hi, (int)e);
             }
-        } else if (ok) {
-            atomicMin(&tmp[j].err_lo, (int)e);
-            atomicMax(&tmp[j].err_hi, (int)e);
         }
     }
 }
