@@ -86,21 +86,39 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(SortSource src, uint64_t
     for (int p = 0; p < kPasses; ++p) { last[p] = 0; run[p] = 0; }
     bool bad = false;
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
-        uint64_t k;
+    // four elements of the grid stride per iteration, their loads issued together
+    for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        uint64_t kk[4];
         if (src.points) {
-            int2 p = src.points[i];
-            bad |= !point_in_domain(p.x, p.y);
-            k = curve_key(CURVE, &tb, (uint32_t)p.x & (kSide - 1), (uint32_t)p.y & (kSide - 1));
+            int2 pt[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = i0 + u * stride;
+                pt[u] = i < n ? __ldg(src.points + i) : make_int2(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bad |= i0 + u * stride < n && !point_in_domain(pt[u].x, pt[u].y);
+                kk[u] = curve_key(CURVE, &tb, (uint32_t)pt[u].x & (kSide - 1), (uint32_t)pt[u].y & (kSide - 1));
+            }
         } else {
-            k = src.keys[i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = i0 + u * stride;
+                kk[u] = i < n ? __ldg(src.keys + i) : 0;
+            }
         }
 #pragma unroll
-        for (int p = 0; p < kPasses; ++p) {
-            uint32_t d = (uint32_t)(k >> (kBits * p)) & (kRadix - 1);
-            if (d != last[p] && run[p]) { atomicAdd(&h[p][last[p]], run[p]); run[p] = 0; }
-            last[p] = d;
-            ++run[p];
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u * stride >= n) break;
+            const uint64_t k = kk[u];
+#pragma unroll
+            for (int p = 0; p < kPasses; ++p) {
+                uint32_t d = (uint32_t)(k >> (kBits * p)) & (kRadix - 1);
+                if (d != last[p] && run[p]) { atomicAdd(&h[p][last[p]], run[p]); run[p] = 0; }
+                last[p] = d;
+                ++run[p];
+            }
         }
     }
 #pragma unroll
@@ -379,7 +397,7 @@ sfc_status radix_sort(const SortSource& src, uint64_t n, const SortDest& dst, So
 
     const int curve = src.points ? src.curve : dst.curve;
     int hgrid = (int)((n + kThreads * 8 - 1) / (kThreads * 8));
-    if (hgrid > num_sms() * 4) hgrid = num_sms() * 4;
+    if (hgrid > num_sms() * 8) hgrid = num_sms() * 8;
     if (curve == SFC_CURVE_HILBERT)
         hist_kernel<SFC_CURVE_HILBERT><<<hgrid, kThreads, 0, st>>>(src, n, sm, status);
     else
