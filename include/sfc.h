@@ -263,7 +263,7 @@ sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm);
 /* The cover currently used by queries (0, 1 or 2), or -1 for idx == NULL. */
 int sfc_cover_refine(const sfc_index* idx);
 
-/* Interval slots per query of the current cover: 4, 9 or 25 (0 for idx == NULL); the stride
+/* Interval slots per query of the current cover: 4, 9 or 25 (3-D: 8 or 27; 0 for idx == NULL); the stride
  * of sfc_query_ranges' outputs. */
 int sfc_query_max_intervals(const sfc_index* idx);
 

@@ -1,18 +1,21 @@
 // Batched distance query (Alg. 1 for m queries at once).
 //
-//   plan_kernel    one thread per query: bounding square Q of B_delta(q), the level l with
+//   plan_kernel    one thread per query (in curve order of the centres when the queries are
+//                  reordered): bounding square Q of B_delta(q), the level l with
 //                  2 delta <= 2^l < 4 delta, the <= 4 cells of cells(Q) and their key
 //                  intervals [pi(C)o0, pi(C)o1] (Observation) -- or, with a refined cover,
-//                  the cells one or two levels finer (<= 9 / <= 25) that meet the ball --
-//                  sorted and with abutting intervals merged, then lower_bound of both ends
-//                  of every interval, by binary search or by the learned model (verified,
-//                  with fallback).  The query's scan length S_q is cut into chunks of C
-//                  points.
+//                  the cells one or two levels finer (<= 9 / <= 25) that meet the window;
+//                  cells the early-termination bitmap shows empty are dropped -- sorted and
+//                  with abutting intervals merged, then lower_bound of both ends of every
+//                  interval, by binary search or by the learned model (fence bracket and
+//                  error window, verified, with fallback).  The query's scan length S_q is cut
+//                  into chunks of C points.  plan3_kernel does the same for 3-D points.
 //   scan           exclusive scan of the chunk counts -> chunk bases.
 //   count_kernel   persistent warps take batches of chunks from a counter (work stealing);
-//                  a warp streams the chunk's coordinates, applies the exact int64 filter
-//                  dx^2 + dy^2 <= delta^2, keeps the warp ballots as a hit bitmask (one bit
-//                  per scanned point) and adds the chunk's popcount to the query's count.
+//                  a warp streams the chunk's coordinates, applies the exact window test
+//                  (disc dx^2 + dy^2 <= delta^2 in int64, square, or 3-D ball), keeps the warp
+//                  ballots as a hit bitmask (one bit per scanned point) and adds the chunk's
+//                  popcount to the query's count.
 //   scan           exclusive scan of the per-query counts -> the caller's out_offsets.
 //   write_kernel   persistent warps take batches of queries; a warp walks its query's
 //                  chunks in order, reads the bitmask (or, past the bitmask budget, re-runs

@@ -17,7 +17,7 @@ struct QueryArgs {
     const int32_t* delta;        // [m]
     uint64_t m;
     uint32_t* ranges;            // [m][2 * kint]: (begin, end) of up to kint intervals
-    uint32_t kint;               // intervals stored per query (4, 9 or 25 by the cover)
+    uint32_t kint;               // intervals stored per query (2-D: 4, 9 or 25 by the cover; 3-D: 8 or 27)
     int drop;                    // cover refinement: 0 cells(Q), 1 or 2 levels finer
     int norm;                    // SFC_NORM_DISC or SFC_NORM_SQUARE
     uint32_t* nchunks;           // [m]
