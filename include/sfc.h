@@ -72,7 +72,7 @@ typedef struct sfc_index sfc_index;   /* opaque; owned by the library */
 typedef struct {
     sfc_bounds bounds;      /* bound search used by queries (default SFC_BOUNDS_BINARY) */
     int leaves;             /* learned model: number of leaf segments (default 4096) */
-    int train_steps;        /* learned model: Adam steps of the root (default 25) */
+    int train_steps;        /* learned model: Adam steps of the root (default 8) */
     int train_samples;      /* learned model: keys sampled for root training (default 16384) */
     float learning_rate;    /* learned model: Adam step size (default 0.02) */
     int chunk;              /* scan chunk in points (0 = autotuned/default 1024) */

@@ -329,7 +329,7 @@ void sfc_default_options(sfc_options* opt)
     if (!opt) return;
     opt->bounds = SFC_BOUNDS_BINARY;
     opt->leaves = 4096;
-    opt->train_steps = 25;
+    opt->train_steps = 8;
     opt->train_samples = 16384;
     opt->learning_rate = 0.02f;
     opt->chunk = 0;
