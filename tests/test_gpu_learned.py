@@ -69,7 +69,7 @@ def test_adam_step_matches_oracle(cuda, npar):
 @pytest.mark.parametrize("root", ["mlp", "pwl"])
 def test_training_lowers_the_loss(cuda, root):
     wl = W.normal_uniform_queries(200_000, 1, 0.001)
-    idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned", root=root)
+    idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned", root=root, train_steps=25)
     model = sfc.sfc_model_get(idx)
     assert model["root"] == root
     ref = oracle.build(wl.points)
