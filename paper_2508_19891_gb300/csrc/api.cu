@@ -284,15 +284,12 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     return SFC_OK;
 }
 
-sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
-                    const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t cap, cudaStream_t st)
+// The write pass for the queries [q_begin, q_end) of the pending count (no state checks).
+sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                          const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t cap, cudaStream_t st,
+                          uint64_t q_begin, uint64_t q_end)
 {
     QueryWs& w = idx->qws;
-    if (!w.pending.valid || w.pending.q != d_q || w.pending.delta != d_delta || w.pending.m != m ||
-        w.pending.offsets != d_out_offsets)
-        return SFC_ERR_STATE;
-    w.pending.valid = false;
-    if (m == 0) return SFC_OK;
     QueryArgs a = base_args(idx, d_q, d_delta, m);
     a.drop = w.pending.drop;
     a.kint = (uint32_t)query_intervals(idx->dim, a.drop);
@@ -314,10 +311,24 @@ sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
         a.wbase = w.wbase.as<uint64_t>();
     }
     a.ids_capacity = d_out_ids ? cap : 0;
+    a.q_begin = q_begin;
+    a.q_end = q_end;
     // the write pass's own work counter starts at zero (a repeated write stays correct)
     SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + 1, 0, sizeof(unsigned long long), st));
     ProfScope ps(idx, "write", st);
     return launch_write(a, st);
+}
+
+sfc_status do_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
+                    const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t cap, cudaStream_t st)
+{
+    QueryWs& w = idx->qws;
+    if (!w.pending.valid || w.pending.q != d_q || w.pending.delta != d_delta || w.pending.m != m ||
+        w.pending.offsets != d_out_offsets)
+        return SFC_ERR_STATE;
+    w.pending.valid = false;
+    if (m == 0) return SFC_OK;
+    return do_write_range(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, cap, st, 0, m);
 }
 
 }  // namespace
@@ -776,9 +787,33 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
         return SFC_ERR_CAPACITY;
     }
     SFC_TRY(hs.ids.ensure(total * sizeof(uint32_t), st));
-    SFC_TRY(do_write(idx, dq, dd, m, doff, hs.ids.as<uint32_t>(), total, st));
+    uint32_t* d_ids = hs.ids.as<uint32_t>();
+    const int S = HostStage::kSlices;
+    if (!idx->qws.pending.ordered && m >= (uint64_t)S && total * sizeof(uint32_t) >= (32ull << 20)) {
+        // the write pass in query slices; the ids of each finished slice go out on a second
+        // stream while the next slices are written (output offsets are in query order)
+        if (!hs.copy) {
+            SFC_CUDA_TRY(cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking));
+            for (auto& e : hs.done) SFC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        idx->qws.pending.valid = false;
+        for (int sl = 0; sl < S; ++sl) {
+            const uint64_t qa = m * (uint64_t)sl / S, qb = m * (uint64_t)(sl + 1) / S;
+            SFC_TRY(do_write_range(idx, dq, dd, m, doff, d_ids, total, st, qa, qb));
+            SFC_CUDA_TRY(cudaEventRecord(hs.done[sl], st));
+            SFC_CUDA_TRY(cudaStreamWaitEvent(hs.copy, hs.done[sl], 0));
+            const uint64_t a = h_out_offsets[qa], b = h_out_offsets[qb];
+            if (b > a)
+                SFC_CUDA_TRY(cudaMemcpyAsync(h_out_ids + a, d_ids + a, (b - a) * sizeof(uint32_t),
+                                             cudaMemcpyDeviceToHost, hs.copy));
+        }
+        SFC_CUDA_TRY(cudaStreamSynchronize(hs.copy));
+        SFC_CUDA_TRY(cudaStreamSynchronize(st));
+        return SFC_OK;
+    }
+    SFC_TRY(do_write(idx, dq, dd, m, doff, d_ids, total, st));
     if (total)
-        SFC_CUDA_TRY(cudaMemcpyAsync(h_out_ids, hs.ids.ptr, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        SFC_CUDA_TRY(cudaMemcpyAsync(h_out_ids, d_ids, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     SFC_CUDA_TRY(cudaStreamSynchronize(st));
     return SFC_OK;
 }

@@ -26,7 +26,10 @@ struct QueryWs {
 };
 
 struct HostStage {          // device staging of sfc_query_batch_host
+    static constexpr int kSlices = 8;   // write-pass slices whose ids are copied out as they finish
     DevBuf q, delta, offsets, ids;
+    cudaStream_t copy = nullptr;        // stream of the device-to-host copies of the ids
+    cudaEvent_t done[kSlices] = {};     // slice s written
 };
 
 struct ModelState {

@@ -815,12 +815,13 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
         set_status(a.status, SFC_DEV_CAPACITY);
     const uint32_t W = a.chunk >> 5;
+    const uint64_t qe = a.q_end ? a.q_end : a.m;
     while (true) {
         uint64_t q0 = 0;
         if (lane == 0) q0 = atomicAdd(a.work_ctr + 1, (unsigned long long)a.qbatch);
-        q0 = __shfl_sync(0xffffffffu, q0, 0);
-        if (q0 >= a.m) break;
-        const uint64_t q1 = min(a.m, q0 + a.qbatch);
+        q0 = a.q_begin + __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= qe) break;
+        const uint64_t q1 = min(qe, q0 + a.qbatch);
         for (uint64_t r = q0; r < q1; ++r) {
             const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
             const uint32_t k = __ldg(a.counts + q);

@@ -32,6 +32,7 @@ struct QueryArgs {
     uint64_t* out_offsets;       // [m + 1]
     uint32_t* out_ids;
     uint64_t ids_capacity;
+    uint64_t q_begin, q_end;     // write pass: the queries [q_begin, q_end) (q_end 0: all m)
     uint32_t* status;
     unsigned long long* scanned;   // sum of S_q over the batch (statistics)
     // optional processing order: queries handed out in curve order of their centres

@@ -197,6 +197,15 @@ void release_index(sfc_index* idx, cudaStream_t st)
     q.nch_sorted.release(st); q.wbase.release(st);
     HostStage& h = idx->stage;
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
+    if (h.copy) {
+        cudaStreamSynchronize(h.copy);
+        cudaStreamDestroy(h.copy);
+        h.copy = nullptr;
+        for (auto& e : h.done) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
+    }
     ModelState& M = idx->model;
     M.state.release(st); M.samples.release(st); M.partial.release(st);
     M.tmp.release(st); M.leaves.release(st); M.route.release(st); M.fence.release(st);

@@ -201,6 +201,25 @@ def test_host_buffer_api_pinned_output(cuda):
     assert np.array_equal(ids, rids)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_api_sliced_copy(cuda, pinned):
+    """A batch with more than 32 MB of ids: the write pass runs in query slices and each
+    slice's ids are copied out on a second stream while the next are written."""
+    wl = W.mixed_1e7(scale=0.05)
+    idx = sfc.sfc_build_host(wl.points, "z", bounds="learned", cover_refine=1)
+    roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta, threads=8)
+    total = int(roff[-1])
+    assert total * 4 >= 32 << 20
+    if pinned:
+        out = torch.full((total,), -1, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    else:
+        out = np.full(total, 7, np.uint32)
+    for _ in range(2):
+        off, ids = sfc.sfc_query_batch_host(idx, wl.queries, wl.delta, total, out_ids=out)
+        assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+    assert sfc.sfc_device_status(idx) == (0, 0)
+
+
 def test_roads_scaled(cuda):
     wl = W.roads_3e7(scale=0.005)
     assert_same(wl.points, wl.queries, wl.delta, "h", cuda)
