@@ -178,6 +178,8 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
     SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
+    SFC_TRY(w.small_list.ensure(m * sizeof(uint32_t), st));
+    SFC_TRY(w.small_mask.ensure(m * sizeof(unsigned long long), st));
     if (idx->opt.reorder_queries != 0 && idx->dim == 2) {
         SFC_TRY(w.qkeys.ensure(m * sizeof(uint64_t), st));
         SFC_TRY(w.qkeys_sorted.ensure(m * sizeof(uint64_t), st));
@@ -236,6 +238,8 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.batch = idx->batch;
     a.qbatch = idx->qbatch;
     a.work_ctr = w.ctr.as<unsigned long long>();
+    a.small_list = w.small_list.as<uint32_t>();
+    a.small_mask = w.small_mask.as<unsigned long long>();
     a.out_offsets = d_out_offsets;
     a.scanned = scan_stats(idx);
     // per-batch statistics: learned-bounds counters and the scanned total
@@ -304,6 +308,8 @@ sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_d
     a.batch = idx->batch;
     a.qbatch = idx->qbatch;
     a.work_ctr = w.ctr.as<unsigned long long>();
+    a.small_list = w.small_list.as<uint32_t>();
+    a.small_mask = w.small_mask.as<unsigned long long>();
     a.out_offsets = const_cast<uint64_t*>(d_out_offsets);
     a.out_ids = d_out_ids;
     if (w.pending.ordered) {

@@ -21,6 +21,7 @@ struct PendingCount {       // plan kept between sfc_query_count and sfc_query_w
 
 struct QueryWs {
     DevBuf ranges, nchunks, chunk_base, counts, masks, ctr;
+    DevBuf small_list, small_mask;   // queries of the small-query path and their hit masks
     DevBuf qkeys, qkeys_sorted, perm, nch_sorted, wbase;   // curve-order processing
     PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false, 0, 0};
 };

@@ -328,6 +328,19 @@ __device__ __forceinline__ int query_bounds(const Bounds& bounds, const QueryArg
     return cnt;
 }
 
+// Lists query i as small (it scans at most kSmallScan points) for the thread-per-query kernels;
+// one atomic per warp.  Every lane of the warp calls.
+__device__ __forceinline__ void small_append(const QueryArgs& a, bool small, uint64_t i)
+{
+    const uint32_t mask = __ballot_sync(0xffffffffu, small);
+    if (!mask) return;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(a.work_ctr + 2, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (small) a.small_list[base + __popc(mask & lanemask_lt())] = (uint32_t)i;
+}
+
 // Optional outputs of the plan (the ranges export); null in the query path.
 struct PlanExport {
     uint64_t* lo;
@@ -395,12 +408,14 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
             }
         }
     }
+    const bool small = !EXPORT && a.small_list && active && S > 0 && S <= kSmallScan;
+    if (!EXPORT && a.small_list) small_append(a, small, i);
     if (!active) return;
     if (!EXPORT) {
         uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * K * i);
 #pragma unroll
         for (int k = 0; k < K; ++k) rp[k] = k < cnt ? make_uint2(b[k], e[k]) : make_uint2(0u, 0u);
-        a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+        a.nchunks[i] = small ? 0u : (uint32_t)((S + a.chunk - 1) / a.chunk);
     } else {
         for (int k = 0; k < K; ++k) {
             const bool u = k < cnt;
@@ -532,12 +547,14 @@ __global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExp
             if (a.cells && tc) atomicAdd(a.cells, tc);
         }
     }
+    const bool small = !EXPORT && a.small_list && active && S > 0 && S <= kSmallScan;
+    if (!EXPORT && a.small_list) small_append(a, small, i);
     if (!active) return;
     if (!EXPORT) {
         uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * kCells3 * i);
 #pragma unroll
         for (int k = 0; k < kCells3; ++k) rp[k] = k < cnt ? make_uint2(b[k], e[k]) : make_uint2(0u, 0u);
-        a.nchunks[i] = (uint32_t)((S + a.chunk - 1) / a.chunk);
+        a.nchunks[i] = small ? 0u : (uint32_t)((S + a.chunk - 1) / a.chunk);
     } else {
         for (int k = 0; k < kCells3; ++k) {
             const bool u = k < cnt;
@@ -800,6 +817,77 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 }
 
 // ------------------------------------------------------------------------------------
+// small queries: one thread per query
+// ------------------------------------------------------------------------------------
+// A query that scans at most kSmallScan points would spend most of a warp's time in the
+// chunked passes on its per-query setup; one thread walks its intervals instead, keeping hit
+// f (the f-th scanned point, in scan order) as bit f of a 64-bit mask.
+__device__ __forceinline__ QView small_view(const QueryArgs& a, uint64_t qi)
+{
+    QView v;
+    v.S = 0;
+    v.nint = a.kint;
+    if (a.dim == 3) {
+        v.q = make_int2(__ldg(a.q + 3 * qi), __ldg(a.q + 3 * qi + 1));
+        v.qz = __ldg(a.q + 3 * qi + 2);
+    } else {
+        v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
+        v.qz = 0;
+    }
+    v.d = __ldg(a.delta + qi);
+    v.d2 = (int64_t)v.d * v.d;
+    return v;
+}
+
+template <int GEOM>
+__global__ void __launch_bounds__(kThreads) small_count_kernel(QueryArgs a)
+{
+    using P = typename Geom<GEOM>::P;
+    const P* __restrict__ xy = Geom<GEOM>::points(a);
+    const uint64_t ns = a.work_ctr[2];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += stride) {
+        const uint32_t q = a.small_list[t];
+        const QView v = small_view(a, q);
+        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
+        unsigned long long mask = 0;
+        uint32_t f = 0;
+        for (uint32_t r = 0; r < a.kint; ++r) {
+            const uint2 be = __ldg(rp + r);
+            for (uint32_t pos = be.x; pos < be.y; ++pos, ++f)
+                if (is_hit<GEOM>(v, __ldg(xy + pos))) mask |= 1ull << f;
+        }
+        a.small_mask[t] = mask;
+        a.counts[q] = (uint32_t)__popcll(mask);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) small_write_kernel(QueryArgs a)
+{
+    const uint64_t ns = a.work_ctr[2];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t qe = a.q_end ? a.q_end : a.m;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += stride) {
+        const unsigned long long mask = a.small_mask[t];
+        if (!mask) continue;
+        const uint32_t q = a.small_list[t];
+        if (a.perm == nullptr && (q < a.q_begin || q >= qe)) continue;   // a slice of the queries
+        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
+        uint64_t dst = a.out_offsets[q];
+        uint32_t f = 0;
+        for (uint32_t r = 0; r < a.kint && (mask >> f); ++r) {
+            const uint2 be = __ldg(rp + r);
+            for (uint32_t pos = be.x; pos < be.y; ++pos, ++f) {
+                if ((mask >> f) & 1ull) {
+                    if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
+                    ++dst;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // write_kernel
 // ------------------------------------------------------------------------------------
 template <int WPL, int GEOM>
@@ -924,6 +1012,22 @@ void launch_count_write_geom(const QueryArgs& a, bool write, cudaStream_t st)
     }
 }
 
+// Thread-per-query kernels for the small queries (their number is read on the device).
+void launch_small(const QueryArgs& a, bool write, cudaStream_t st)
+{
+    const unsigned g = (unsigned)std::min<uint64_t>((a.m + kThreads - 1) / kThreads, (uint64_t)num_sms() * 8);
+    if (write) {
+        small_write_kernel<<<g, kThreads, 0, st>>>(a);
+    } else if (a.dim == 3) {
+        small_count_kernel<kGeomBall3><<<g, kThreads, 0, st>>>(a);
+    } else if (a.norm == SFC_NORM_SQUARE) {
+        small_count_kernel<kGeomSquare><<<g, kThreads, 0, st>>>(a);
+    } else {
+        small_count_kernel<kGeomDisc><<<g, kThreads, 0, st>>>(a);
+    }
+    count_launch();
+}
+
 template <int WPL>
 sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 {
@@ -931,6 +1035,7 @@ sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
     else if (a.norm == SFC_NORM_SQUARE) launch_count_write_geom<WPL, kGeomSquare>(a, write, st);
     else launch_count_write_geom<WPL, kGeomDisc>(a, write, st);
     count_launch();
+    if (a.small_list) launch_small(a, write, st);
     return launch_status();
 }
 

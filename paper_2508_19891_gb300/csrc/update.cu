@@ -194,7 +194,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     q.ranges.release(st); q.nchunks.release(st); q.chunk_base.release(st);
     q.counts.release(st); q.masks.release(st); q.ctr.release(st);
     q.qkeys.release(st); q.qkeys_sorted.release(st); q.perm.release(st);
-    q.nch_sorted.release(st); q.wbase.release(st);
+    q.nch_sorted.release(st); q.wbase.release(st); q.small_list.release(st); q.small_mask.release(st);
     HostStage& h = idx->stage;
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
     if (h.copy) {

@@ -220,6 +220,27 @@ def test_host_buffer_api_sliced_copy(cuda, pinned):
     assert sfc.sfc_device_status(idx) == (0, 0)
 
 
+@pytest.mark.parametrize("curve", ["z", "h"])
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_small_query_boundary(cuda, curve, reorder):
+    """Queries that scan at most 64 points are counted and written one thread each: a stack
+    of 64 equal points and one of 65, both queried with delta 0 (every scanned point a hit),
+    plus scans of a few points among a background, equal the oracle on both sides of 64."""
+    rng = np.random.default_rng(21)
+    bg = rng.integers(0, 1 << 30, size=(5000, 2), dtype=np.int64)
+    a, b = (1 << 20, 3 << 22), (5 << 25, 7 << 21)
+    pts = np.concatenate([bg, np.tile(a, (64, 1)), np.tile(b, (65, 1))]).astype(np.int32)
+    pts = pts[rng.permutation(len(pts))]
+    qs = np.concatenate([[a, b, a, b], bg[:300]]).astype(np.int32)
+    d = np.concatenate([[0, 0, 1, 1], rng.integers(0, 1 << 16, 300)]).astype(np.int32)
+    for bounds in ("binary", "learned"):
+        idx, st = assert_same(pts, qs, d, curve, cuda, bounds=bounds, reorder_queries=reorder)
+        assert st == (0, 0)
+    ref = oracle.build(pts, 30, curve)
+    roff, _ = oracle.query(ref, qs, d)
+    assert roff[1] - roff[0] == 64 and roff[2] - roff[1] == 65
+
+
 def test_roads_scaled(cuda):
     wl = W.roads_3e7(scale=0.005)
     assert_same(wl.points, wl.queries, wl.delta, "h", cuda)
