@@ -179,7 +179,7 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
     SFC_TRY(w.small_list.ensure(m * sizeof(uint32_t), st));
-    SFC_TRY(w.small_mask.ensure(m * sizeof(unsigned long long), st));
+    SFC_TRY(w.small_mask.ensure(m * kSmallWords * sizeof(unsigned long long), st));
     if (idx->opt.reorder_queries != 0 && idx->dim == 2) {
         SFC_TRY(w.qkeys.ensure(m * sizeof(uint64_t), st));
         SFC_TRY(w.qkeys_sorted.ensure(m * sizeof(uint64_t), st));

@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 // ------------------------------------------------------------------------------------
 // A query that scans at most kSmallScan points would spend most of a warp's time in the
 // chunked passes on its per-query setup; one thread walks its intervals instead, keeping hit
-// f (the f-th scanned point, in scan order) as bit f of a 64-bit mask.
+// f (the f-th scanned point, in scan order) as bit f mod 64 of mask word f / 64.
 __device__ __forceinline__ QView small_view(const QueryArgs& a, uint64_t qi)
 {
     QView v;
@@ -843,6 +843,7 @@ template <int GEOM>
 __global__ void __launch_bounds__(kThreads) small_count_kernel(QueryArgs a)
 {
     using P = typename Geom<GEOM>::P;
+    constexpr uint32_t NW = kSmallWords;
     const P* __restrict__ xy = Geom<GEOM>::points(a);
     const uint64_t ns = a.work_ctr[2];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -850,38 +851,53 @@ __global__ void __launch_bounds__(kThreads) small_count_kernel(QueryArgs a)
         const uint32_t q = a.small_list[t];
         const QView v = small_view(a, q);
         const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
-        unsigned long long mask = 0;
-        uint32_t f = 0;
+        unsigned long long* mw = a.small_mask + t * NW;
+        unsigned long long word = 0;
+        uint32_t f = 0, hits = 0;
         for (uint32_t r = 0; r < a.kint; ++r) {
             const uint2 be = __ldg(rp + r);
-            for (uint32_t pos = be.x; pos < be.y; ++pos, ++f)
-                if (is_hit<GEOM>(v, __ldg(xy + pos))) mask |= 1ull << f;
+            for (uint32_t pos = be.x; pos < be.y; ++pos) {
+                if (is_hit<GEOM>(v, __ldg(xy + pos))) word |= 1ull << (f & 63);
+                if ((++f & 63) == 0) {   // a full word of 64 scanned points
+                    mw[(f >> 6) - 1] = word;
+                    hits += __popcll(word);
+                    word = 0;
+                }
+            }
         }
-        a.small_mask[t] = mask;
-        a.counts[q] = (uint32_t)__popcll(mask);
+        if (f & 63) {
+            mw[f >> 6] = word;
+            hits += __popcll(word);
+        }
+        a.counts[q] = hits;
     }
 }
 
 __global__ void __launch_bounds__(kThreads) small_write_kernel(QueryArgs a)
 {
+    constexpr uint32_t NW = kSmallWords;
     const uint64_t ns = a.work_ctr[2];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t qe = a.q_end ? a.q_end : a.m;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += stride) {
-        const unsigned long long mask = a.small_mask[t];
-        if (!mask) continue;
         const uint32_t q = a.small_list[t];
         if (a.perm == nullptr && (q < a.q_begin || q >= qe)) continue;   // a slice of the queries
+        uint32_t left = __ldg(a.counts + q);
+        if (left == 0) continue;
+        const unsigned long long* mw = a.small_mask + t * NW;
         const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
         uint64_t dst = a.out_offsets[q];
+        unsigned long long word = mw[0];
         uint32_t f = 0;
-        for (uint32_t r = 0; r < a.kint && (mask >> f); ++r) {
+        for (uint32_t r = 0; r < a.kint && left; ++r) {
             const uint2 be = __ldg(rp + r);
-            for (uint32_t pos = be.x; pos < be.y; ++pos, ++f) {
-                if ((mask >> f) & 1ull) {
+            for (uint32_t pos = be.x; pos < be.y && left; ++pos) {
+                if ((word >> (f & 63)) & 1ull) {
                     if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
                     ++dst;
+                    --left;
                 }
+                if ((++f & 63) == 0 && left) word = mw[f >> 6];
             }
         }
     }

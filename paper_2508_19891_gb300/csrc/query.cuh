@@ -31,7 +31,7 @@ struct QueryArgs {
     unsigned long long* work_ctr;  // [0] count-pass queue, [1] write-pass queue, [2] small queries
     // queries that scan at most kSmallScan points skip the chunked passes: the plan lists them
     // (small_list[0 .. work_ctr[2])) and thread-per-query kernels count and write them, keeping
-    // each one's hits as a 64-bit mask (NULL: no small-query path)
+    // each one's hits as kSmallWords mask words (NULL: no small-query path)
     uint32_t* small_list;
     unsigned long long* small_mask;
     uint64_t* out_offsets;       // [m + 1]
@@ -60,7 +60,10 @@ sfc_status launch_plan(const QueryArgs& a, const LearnedModelView* lm, cudaStrea
 int cover_intervals(int drop);   // intervals stored per query for a cover refinement
 int query_intervals(int dim, int drop);   // ... for an index of dimension dim
 sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
-constexpr uint32_t kSmallScan = 64;   // scan length up to which a query takes the small-query path
+// scan length up to which a query takes the small-query path, and its mask words (one per 64
+// scanned points)
+constexpr uint32_t kSmallScan = 64;
+constexpr uint32_t kSmallWords = (kSmallScan + 63) / 64;
 // curve key of each query centre (invalid centres sort last) with the query index as value
 sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);
 // out[r] = nchunks[perm[r]]
