@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(PassArgs a)
             uint32_t fl = (uint32_t)(w >> 32) & 3u;
             if (ep != epoch || fl == 0) {
                 if (++spins > kSpinLimit) { set_status(a.status, SFC_DEV_TIMEOUT); break; }
+                __nanosleep(32);   // not published yet: leave the issue slots to other warps
                 continue;
             }
             excl += (uint32_t)w;
