@@ -973,13 +973,21 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
                     // grow with t, so its interval cursor only moves forward
                     const uint32_t gbase = s0 + (uint32_t)s * 1024u;
                     const uint64_t dst0 = off + rank;
+                    if (dst0 + K <= a.ids_capacity) {   // the whole group fits: no per-id check
+                        uint32_t* __restrict__ out = a.out_ids + dst0;
 #pragma unroll 4
-                    for (uint32_t t = lane; t < K; t += 32) {
-                        const uint32_t f = gbase + buf[t];
-                        if (f >= end) seek(tab, v.nint, f, cr, shift, end);
-                        const uint64_t dst = dst0 + t;
-                        const uint32_t id = __ldg(a.ids + (f + shift));
-                        if (dst < a.ids_capacity) __stcs(a.out_ids + dst, id);   // written once, not re-read
+                        for (uint32_t t = lane; t < K; t += 32) {
+                            const uint32_t f = gbase + buf[t];
+                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
+                            __stcs(out + t, __ldg(a.ids + (f + shift)));   // written once, not re-read
+                        }
+                    } else {
+                        for (uint32_t t = lane; t < K; t += 32) {
+                            const uint32_t f = gbase + buf[t];
+                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
+                            const uint64_t dst = dst0 + t;
+                            if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + (f + shift));
+                        }
                     }
                     __syncwarp();
                     rank += K;
