@@ -929,13 +929,13 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
         for (uint64_t r = q0; r < q1; ++r) {
             const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
             const uint32_t k = __ldg(a.counts + q);
-            if (k == 0) continue;
+            const uint64_t cb = __ldg(a.chunk_base + q);
+            const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
+            if (k == 0 || nch == 0) continue;   // no hits, or a query of the small-query path
             const QView v = load_query(a, q, tab);
             uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
             uint32_t shift = 0, end = 0;
             const uint64_t off = a.out_offsets[q];
-            const uint64_t cb = __ldg(a.chunk_base + q);
-            const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
             uint32_t rank = 0;
             for (uint64_t j = 0; j < nch && rank < k; ++j) {
                 const uint64_t g = cb + j;
