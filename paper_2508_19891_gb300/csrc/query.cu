@@ -681,34 +681,20 @@ __device__ __forceinline__ bool is_hit(const QView& v, int4 p)
     return s <= v.d2;
 }
 
-// Stores ballot words w0..w3 (points s0 + 32 * (it + u) ...) in lanes it % 32 .. it % 32 + 3 of
-// slot it / 32.
-template <int WPL>
-__device__ __forceinline__ void keep_words(uint32_t (&words)[WPL], uint32_t it, uint32_t w0, uint32_t w1,
-                                           uint32_t w2, uint32_t w3)
-{
-    const uint32_t d = lane_id() - (it & 31);
-    if (d < 4) {
-        const uint32_t w = d == 0 ? w0 : d == 1 ? w1 : d == 2 ? w2 : w3;
-        const uint32_t slot = it >> 5;
-#pragma unroll
-        for (int s = 0; s < WPL; ++s)
-            if (slot == (uint32_t)s) words[s] = w;
-    }
-}
-
 // Filters points [s0, s1) of the query's concatenated intervals; returns the hit count and
-// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.  Points go in
-// groups of 4 x 32: when the whole group lies inside the chunk and no lane crosses the end of
-// its interval (one vote), the group runs without per-point guards; otherwise each point is
-// checked and the lane looks its interval up again when it crosses into the next one.
+// leaves word w (the ballot of points s0 + 32w ...) in lane w % 32, slot w / 32.  Lane 0 keeps
+// each step's four ballots in the warp's word buffer sw (WPL x 32 words, one 16-byte store),
+// and every lane reads its own words back at the end.  Points go in groups of 4 x 32: when the
+// whole group lies inside the chunk and no lane crosses the end of its interval (one vote), the
+// group runs without per-point guards; otherwise each point is checked and the lane looks its
+// interval up again when it crosses into the next one.
 template <int WPL, int GEOM>
 __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView& v, const WarpTab* tab,
-                                                 uint32_t s0, uint32_t s1, uint32_t (&words)[WPL])
+                                                 uint32_t s0, uint32_t s1, uint32_t (&words)[WPL],
+                                                 uint32_t* __restrict__ sw)
 {
-#pragma unroll
-    for (int s = 0; s < WPL; ++s) words[s] = 0;
     const uint32_t nit = (s1 - s0 + 31) >> 5;
+    __syncwarp();   // the previous chunk's words have been read
     using P = typename Geom<GEOM>::P;
     const P* __restrict__ xy = Geom<GEOM>::points(a);
     uint32_t f = s0 + lane_id();
@@ -723,7 +709,7 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
             const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p1));
             const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p2));
             const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p3));
-            keep_words<WPL>(words, it, w0, w1, w2, w3);
+            if (lane_id() == 0) *reinterpret_cast<uint4*>(sw + it) = make_uint4(w0, w1, w2, w3);
         } else {
             P p[4];
             bool val[4];
@@ -737,8 +723,14 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
             uint32_t w[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) w[u] = __ballot_sync(0xffffffffu, val[u] && is_hit<GEOM>(v, p[u]));
-            keep_words<WPL>(words, it, w[0], w[1], w[2], w[3]);
+            if (lane_id() == 0) *reinterpret_cast<uint4*>(sw + it) = make_uint4(w[0], w[1], w[2], w[3]);
         }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+        const uint32_t wi = s * 32 + lane_id();
+        words[s] = wi < nit ? sw[wi] : 0u;
     }
     uint32_t c = 0;
 #pragma unroll
@@ -774,7 +766,9 @@ template <int WPL, int GEOM>
 __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 {
     __shared__ WarpTab s_tab[kThreads / 32];
+    __shared__ __align__(16) uint32_t s_words[kThreads / 32][WPL * 32];
     WarpTab* tab = &s_tab[threadIdx.x >> 5];
+    uint32_t* sw = s_words[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     // work items are chunks in processing order: wbase (curve order) or chunk_base (input order)
     const uint64_t* wb = a.wbase ? a.wbase : a.chunk_base;
@@ -801,7 +795,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
             const uint32_t s0 = j * a.chunk;
             const uint32_t s1 = min(v.S, s0 + a.chunk);
             uint32_t words[WPL];
-            const uint32_t cnt = filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words);
+            const uint32_t cnt = filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words, sw);
             if (g < a.mask_chunks) {
                 const uint32_t nw = (s1 - s0 + 31) >> 5;
                 uint32_t* mp = a.masks + g * W;
@@ -911,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
 {
     // per-warp staging of one group of 32 mask words (<= 1024 hits): each hit's index within
     // the group's 1024 points, 16 bits; its array position is resolved in the copy loop
-    __shared__ uint16_t s_rel[kThreads / 32][1024];
+    __shared__ __align__(16) uint16_t s_rel[kThreads / 32][1024];
     __shared__ WarpTab s_tab[kThreads / 32];
     uint16_t* buf = s_rel[threadIdx.x >> 5];
     WarpTab* tab = &s_tab[threadIdx.x >> 5];
@@ -951,7 +945,8 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
                         words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
                     }
                 } else {
-                    filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words);
+                    filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words, reinterpret_cast<uint32_t*>(buf));
+                    __syncwarp();   // the words are read before buf takes the staged indices
                 }
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
