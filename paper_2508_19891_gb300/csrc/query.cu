@@ -701,6 +701,27 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
     uint32_t r = 0, shift, end;
     seek(tab, v.nint, f, r, shift, end);
     for (uint32_t it = 0; it < nit; it += 4, f += 128) {
+        if (s0 + (it + 8) * 32 <= s1 && __all_sync(0xffffffffu, f + 224 < end)) {
+            // eight steps inside the chunk and inside every lane's interval
+            const P* p = xy + (f + shift);
+            const P p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
+            const P p4 = __ldg(p + 128), p5 = __ldg(p + 160), p6 = __ldg(p + 192), p7 = __ldg(p + 224);
+            const uint32_t w0 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p0));
+            const uint32_t w1 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p1));
+            const uint32_t w2 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p2));
+            const uint32_t w3 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p3));
+            const uint32_t w4 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p4));
+            const uint32_t w5 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p5));
+            const uint32_t w6 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p6));
+            const uint32_t w7 = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, p7));
+            if (lane_id() == 0) {
+                *reinterpret_cast<uint4*>(sw + it) = make_uint4(w0, w1, w2, w3);
+                *reinterpret_cast<uint4*>(sw + it + 4) = make_uint4(w4, w5, w6, w7);
+            }
+            it += 4;
+            f += 128;
+            continue;
+        }
         const bool full = s0 + (it + 4) * 32 <= s1;     // warp-uniform
         if (full && __all_sync(0xffffffffu, f + 96 < end)) {
             const P* p = xy + (f + shift);
