@@ -701,8 +701,26 @@ __device__ __forceinline__ uint32_t filter_chunk(const QueryArgs& a, const QView
     uint32_t r = 0, shift, end;
     seek(tab, v.nint, f, r, shift, end);
     for (uint32_t it = 0; it < nit; it += 4, f += 128) {
+        // sixteen, eight or four steps that lie inside the chunk and inside every lane's interval
+        // run without per-point guards (sixteen only for the 8-byte 2-D records)
+        if (GEOM != kGeomBall3 && s0 + (it + 16) * 32 <= s1 && __all_sync(0xffffffffu, f + 480 < end)) {
+            const P* p = xy + (f + shift);
+            P pp[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) pp[u] = __ldg(p + 32 * u);
+            uint32_t w[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) w[u] = __ballot_sync(0xffffffffu, is_hit<GEOM>(v, pp[u]));
+            if (lane_id() == 0) {
+#pragma unroll
+                for (int u = 0; u < 16; u += 4)
+                    *reinterpret_cast<uint4*>(sw + it + u) = make_uint4(w[u], w[u + 1], w[u + 2], w[u + 3]);
+            }
+            it += 12;
+            f += 384;
+            continue;
+        }
         if (s0 + (it + 8) * 32 <= s1 && __all_sync(0xffffffffu, f + 224 < end)) {
-            // eight steps inside the chunk and inside every lane's interval
             const P* p = xy + (f + shift);
             const P p0 = __ldg(p), p1 = __ldg(p + 32), p2 = __ldg(p + 64), p3 = __ldg(p + 96);
             const P p4 = __ldg(p + 128), p5 = __ldg(p + 160), p6 = __ldg(p + 192), p7 = __ldg(p + 224);
