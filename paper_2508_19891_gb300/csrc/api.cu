@@ -177,7 +177,7 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
     SFC_TRY(w.nchunks.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.chunk_base.ensure((m + 1) * sizeof(uint64_t), st));
     SFC_TRY(w.counts.ensure(m * sizeof(uint32_t), st));
-    SFC_TRY(w.ctr.ensure(4 * sizeof(unsigned long long), st));
+    SFC_TRY(w.ctr.ensure(kCtrWords * sizeof(unsigned long long), st));
     SFC_TRY(w.small_list.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.small_mask.ensure(m * kSmallWords * sizeof(unsigned long long), st));
     if (idx->opt.reorder_queries != 0 && idx->dim == 2) {
@@ -245,7 +245,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     // per-batch statistics: learned-bounds counters and the scanned total
     SFC_CUDA_TRY(cudaMemsetAsync(model_stats(idx), 0, 6 * sizeof(unsigned long long), st));
     SFC_CUDA_TRY(cudaMemsetAsync(a.counts, 0, m * sizeof(uint32_t), st));
-    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, 4 * sizeof(unsigned long long), st));
+    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr, 0, kCtrWords * sizeof(unsigned long long), st));
     LearnedModelView lv;
     const bool ordered = use_curve_order(idx, m);
     if (ordered) {
@@ -319,8 +319,8 @@ sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_d
     a.ids_capacity = d_out_ids ? cap : 0;
     a.q_begin = q_begin;
     a.q_end = q_end;
-    // the write pass's own work counter starts at zero (a repeated write stays correct)
-    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + 1, 0, sizeof(unsigned long long), st));
+    // the write pass's own work counters start at zero (a repeated write stays correct)
+    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + kCtrWrite, 0, 2 * sizeof(unsigned long long), st));
     ProfScope ps(idx, "write", st);
     return launch_write(a, st);
 }

@@ -336,7 +336,7 @@ __device__ __forceinline__ void small_append(const QueryArgs& a, bool small, uin
     if (!mask) return;
     const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(a.work_ctr + 2, (unsigned long long)__popc(mask));
+    if ((int)lane_id() == leader) base = atomicAdd(a.work_ctr + kCtrSmallSize, (unsigned long long)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (small) a.small_list[base + __popc(mask & lanemask_lt())] = (uint32_t)i;
 }
@@ -799,6 +799,105 @@ __device__ __forceinline__ uint64_t owner_query(const uint64_t* __restrict__ bas
 }
 
 // ------------------------------------------------------------------------------------
+// small queries: one thread per query
+// ------------------------------------------------------------------------------------
+// A query that scans at most kSmallScan points would spend most of a warp's time in the
+// chunked passes on its per-query setup; one thread walks its intervals instead, keeping hit
+// f (the f-th scanned point, in scan order) as bit f mod 64 of mask word f / 64.
+__device__ __forceinline__ QView small_view(const QueryArgs& a, uint64_t qi)
+{
+    QView v;
+    v.S = 0;
+    v.nint = a.kint;
+    if (a.dim == 3) {
+        v.q = make_int2(__ldg(a.q + 3 * qi), __ldg(a.q + 3 * qi + 1));
+        v.qz = __ldg(a.q + 3 * qi + 2);
+    } else {
+        v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
+        v.qz = 0;
+    }
+    v.d = __ldg(a.delta + qi);
+    v.d2 = (int64_t)v.d * v.d;
+    return v;
+}
+
+// Each warp claims 32 listed queries at a time from a shared counter, one per lane; the chunked
+// kernels run these loops once their own queue is empty, so the small queries fill the tail.
+template <int GEOM>
+__device__ __forceinline__ void small_count_tail(const QueryArgs& a)
+{
+    using P = typename Geom<GEOM>::P;
+    constexpr uint32_t NW = kSmallWords;
+    const P* __restrict__ xy = Geom<GEOM>::points(a);
+    const uint64_t ns = a.work_ctr[kCtrSmallSize];
+    while (true) {
+        unsigned long long t0 = 0;
+        if (lane_id() == 0) t0 = atomicAdd(a.work_ctr + kCtrSmallCount, 32ull);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= ns) break;
+        const uint64_t t = t0 + lane_id();
+        if (t >= ns) continue;
+        const uint32_t q = a.small_list[t];
+        const QView v = small_view(a, q);
+        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
+        unsigned long long* mw = a.small_mask + t * NW;
+        unsigned long long word = 0;
+        uint32_t f = 0, hits = 0;
+        for (uint32_t r = 0; r < a.kint; ++r) {
+            const uint2 be = __ldg(rp + r);
+            for (uint32_t pos = be.x; pos < be.y; ++pos) {
+                if (is_hit<GEOM>(v, __ldg(xy + pos))) word |= 1ull << (f & 63);
+                if ((++f & 63) == 0) {   // a full word of 64 scanned points
+                    mw[(f >> 6) - 1] = word;
+                    hits += __popcll(word);
+                    word = 0;
+                }
+            }
+        }
+        if (f & 63) {
+            mw[f >> 6] = word;
+            hits += __popcll(word);
+        }
+        a.counts[q] = hits;
+    }
+}
+
+__device__ __forceinline__ void small_write_tail(const QueryArgs& a)
+{
+    constexpr uint32_t NW = kSmallWords;
+    const uint64_t ns = a.work_ctr[kCtrSmallSize];
+    const uint64_t qe = a.q_end ? a.q_end : a.m;
+    while (true) {
+        unsigned long long t0 = 0;
+        if (lane_id() == 0) t0 = atomicAdd(a.work_ctr + kCtrSmallWrite, 32ull);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= ns) break;
+        const uint64_t t = t0 + lane_id();
+        if (t >= ns) continue;
+        const uint32_t q = a.small_list[t];
+        if (a.perm == nullptr && (q < a.q_begin || q >= qe)) continue;   // a slice of the queries
+        uint32_t left = __ldg(a.counts + q);
+        if (left == 0) continue;
+        const unsigned long long* mw = a.small_mask + t * NW;
+        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
+        uint64_t dst = a.out_offsets[q];
+        unsigned long long word = mw[0];
+        uint32_t f = 0;
+        for (uint32_t r = 0; r < a.kint && left; ++r) {
+            const uint2 be = __ldg(rp + r);
+            for (uint32_t pos = be.x; pos < be.y && left; ++pos) {
+                if ((word >> (f & 63)) & 1ull) {
+                    if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
+                    ++dst;
+                    --left;
+                }
+                if ((++f & 63) == 0 && left) word = mw[f >> 6];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // count_kernel
 // ------------------------------------------------------------------------------------
 template <int WPL, int GEOM>
@@ -815,7 +914,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
     const uint32_t W = a.chunk >> 5;   // mask words per chunk
     while (true) {
         uint64_t g0 = 0;
-        if (lane == 0) g0 = atomicAdd(a.work_ctr, (unsigned long long)a.batch);
+        if (lane == 0) g0 = atomicAdd(a.work_ctr + kCtrCount, (unsigned long long)a.batch);
         g0 = __shfl_sync(0xffffffffu, g0, 0);
         if (g0 >= G) break;
         const uint64_t g1 = min(G, g0 + a.batch);
@@ -847,93 +946,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
             if (lane == 0 && cnt) atomicAdd(a.counts + q, cnt);
         }
     }
-}
-
-// ------------------------------------------------------------------------------------
-// small queries: one thread per query
-// ------------------------------------------------------------------------------------
-// A query that scans at most kSmallScan points would spend most of a warp's time in the
-// chunked passes on its per-query setup; one thread walks its intervals instead, keeping hit
-// f (the f-th scanned point, in scan order) as bit f mod 64 of mask word f / 64.
-__device__ __forceinline__ QView small_view(const QueryArgs& a, uint64_t qi)
-{
-    QView v;
-    v.S = 0;
-    v.nint = a.kint;
-    if (a.dim == 3) {
-        v.q = make_int2(__ldg(a.q + 3 * qi), __ldg(a.q + 3 * qi + 1));
-        v.qz = __ldg(a.q + 3 * qi + 2);
-    } else {
-        v.q = __ldg(reinterpret_cast<const int2*>(a.q) + qi);
-        v.qz = 0;
-    }
-    v.d = __ldg(a.delta + qi);
-    v.d2 = (int64_t)v.d * v.d;
-    return v;
-}
-
-template <int GEOM>
-__global__ void __launch_bounds__(kThreads) small_count_kernel(QueryArgs a)
-{
-    using P = typename Geom<GEOM>::P;
-    constexpr uint32_t NW = kSmallWords;
-    const P* __restrict__ xy = Geom<GEOM>::points(a);
-    const uint64_t ns = a.work_ctr[2];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += stride) {
-        const uint32_t q = a.small_list[t];
-        const QView v = small_view(a, q);
-        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
-        unsigned long long* mw = a.small_mask + t * NW;
-        unsigned long long word = 0;
-        uint32_t f = 0, hits = 0;
-        for (uint32_t r = 0; r < a.kint; ++r) {
-            const uint2 be = __ldg(rp + r);
-            for (uint32_t pos = be.x; pos < be.y; ++pos) {
-                if (is_hit<GEOM>(v, __ldg(xy + pos))) word |= 1ull << (f & 63);
-                if ((++f & 63) == 0) {   // a full word of 64 scanned points
-                    mw[(f >> 6) - 1] = word;
-                    hits += __popcll(word);
-                    word = 0;
-                }
-            }
-        }
-        if (f & 63) {
-            mw[f >> 6] = word;
-            hits += __popcll(word);
-        }
-        a.counts[q] = hits;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) small_write_kernel(QueryArgs a)
-{
-    constexpr uint32_t NW = kSmallWords;
-    const uint64_t ns = a.work_ctr[2];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t qe = a.q_end ? a.q_end : a.m;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += stride) {
-        const uint32_t q = a.small_list[t];
-        if (a.perm == nullptr && (q < a.q_begin || q >= qe)) continue;   // a slice of the queries
-        uint32_t left = __ldg(a.counts + q);
-        if (left == 0) continue;
-        const unsigned long long* mw = a.small_mask + t * NW;
-        const uint2* rp = reinterpret_cast<const uint2*>(a.ranges) + (uint64_t)q * a.kint;
-        uint64_t dst = a.out_offsets[q];
-        unsigned long long word = mw[0];
-        uint32_t f = 0;
-        for (uint32_t r = 0; r < a.kint && left; ++r) {
-            const uint2 be = __ldg(rp + r);
-            for (uint32_t pos = be.x; pos < be.y && left; ++pos) {
-                if ((word >> (f & 63)) & 1ull) {
-                    if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + pos);
-                    ++dst;
-                    --left;
-                }
-                if ((++f & 63) == 0 && left) word = mw[f >> 6];
-            }
-        }
-    }
+    if (a.small_list) small_count_tail<GEOM>(a);
 }
 
 // ------------------------------------------------------------------------------------
@@ -955,7 +968,7 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
     const uint64_t qe = a.q_end ? a.q_end : a.m;
     while (true) {
         uint64_t q0 = 0;
-        if (lane == 0) q0 = atomicAdd(a.work_ctr + 1, (unsigned long long)a.qbatch);
+        if (lane == 0) q0 = atomicAdd(a.work_ctr + kCtrWrite, (unsigned long long)a.qbatch);
         q0 = a.q_begin + __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= qe) break;
         const uint64_t q1 = min(qe, q0 + a.qbatch);
@@ -1029,6 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
             }
         }
     }
+    if (a.small_list) small_write_tail(a);
 }
 
 __global__ void query_keys_kernel(const int32_t* __restrict__ q, uint64_t m, int curve, uint64_t* keys)
@@ -1070,22 +1084,6 @@ void launch_count_write_geom(const QueryArgs& a, bool write, cudaStream_t st)
     }
 }
 
-// Thread-per-query kernels for the small queries (their number is read on the device).
-void launch_small(const QueryArgs& a, bool write, cudaStream_t st)
-{
-    const unsigned g = (unsigned)std::min<uint64_t>((a.m + kThreads - 1) / kThreads, (uint64_t)num_sms() * 8);
-    if (write) {
-        small_write_kernel<<<g, kThreads, 0, st>>>(a);
-    } else if (a.dim == 3) {
-        small_count_kernel<kGeomBall3><<<g, kThreads, 0, st>>>(a);
-    } else if (a.norm == SFC_NORM_SQUARE) {
-        small_count_kernel<kGeomSquare><<<g, kThreads, 0, st>>>(a);
-    } else {
-        small_count_kernel<kGeomDisc><<<g, kThreads, 0, st>>>(a);
-    }
-    count_launch();
-}
-
 template <int WPL>
 sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 {
@@ -1093,7 +1091,6 @@ sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
     else if (a.norm == SFC_NORM_SQUARE) launch_count_write_geom<WPL, kGeomSquare>(a, write, st);
     else launch_count_write_geom<WPL, kGeomDisc>(a, write, st);
     count_launch();
-    if (a.small_list) launch_small(a, write, st);
     return launch_status();
 }
 

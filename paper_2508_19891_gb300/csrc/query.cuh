@@ -28,10 +28,11 @@ struct QueryArgs {
     uint32_t chunk;              // points per chunk (multiple of 32, <= 4096)
     uint32_t batch;              // chunks taken per work-queue grab (count pass)
     uint32_t qbatch;             // queries taken per grab (write pass)
-    unsigned long long* work_ctr;  // [0] count-pass queue, [1] write-pass queue, [2] small queries
+    unsigned long long* work_ctr;  // kCtrWords counters, see kCtrCount ... kCtrSmallCount
     // queries that scan at most kSmallScan points skip the chunked passes: the plan lists them
-    // (small_list[0 .. work_ctr[2])) and thread-per-query kernels count and write them, keeping
-    // each one's hits as kSmallWords mask words (NULL: no small-query path)
+    // (small_list[0 .. work_ctr[kCtrSmallSize])) and the count and write kernels, once their
+    // chunked work is claimed, take them one thread per query, keeping each one's hits as
+    // kSmallWords mask words (NULL: no small-query path)
     uint32_t* small_list;
     unsigned long long* small_mask;
     uint64_t* out_offsets;       // [m + 1]
@@ -64,6 +65,11 @@ sfc_status launch_count(const QueryArgs& a, cudaStream_t st);
 // scanned points)
 constexpr uint32_t kSmallScan = 64;
 constexpr uint32_t kSmallWords = (kSmallScan + 63) / 64;
+// work counters of a query batch: the count pass's chunk queue, the write pass's query queue and
+// its small-query queue (adjacent: the write pass clears both), the small-list length, the
+// count pass's small-query queue
+constexpr int kCtrCount = 0, kCtrWrite = 1, kCtrSmallWrite = 2, kCtrSmallSize = 3, kCtrSmallCount = 4;
+constexpr int kCtrWords = 8;
 // curve key of each query centre (invalid centres sort last) with the query index as value
 sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);
 // out[r] = nchunks[perm[r]]
