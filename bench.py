@@ -260,13 +260,23 @@ def run_ours(args, rank, world, local):
     ms_per_step = total_ms / args.steps
     value = job_throughput(m, world, ms_per_step)
     hbm_peak, peak_kind = peaks()
-    # dominant kernel: the count pass (one launch per step)
-    count_runs, count_ms = agg.get("count", (0, float("nan")))
-    count_avg_ms = count_ms / max(count_runs, 1)
+    # the two query kernels (one launch each per step; the small queries run inside them):
+    # count reads the coordinates (x, y[, z] as int32) and writes one mask bit per scanned
+    # point; write reads the mask bit of each scanned point and each hit's id, and writes the
+    # id.  The roofline object reports the one with the longer live time.
     S = stats["scanned"]
-    # coordinates read (x, y[, z] as int32) + one mask bit per scanned point
-    alg_bytes = 4 * dim * S + S // 8
-    achieved = alg_bytes / (count_avg_ms / 1e3) / 1e9
+    H = stats["hits"]
+    kern = {}
+    for name, phase, alg in (("count_kernel", "count", 4 * dim * S + S // 8),
+                             ("write_kernel", "write", 8 * H + S // 8)):
+        runs, ms = agg.get(phase, (0, float("nan")))
+        avg = ms / max(runs, 1)
+        ach = alg / (avg / 1e3) / 1e9
+        kern[name] = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": ach / hbm_peak,
+                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                      "traffic": committed_traffic(name, alg), "algorithmic_bytes": alg, "avg_launch_ms": avg}
+    dominant = max(kern, key=lambda k: kern[k]["avg_launch_ms"])
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -278,11 +288,8 @@ def run_ours(args, rank, world, local):
                    "reorder_queries": opts.get("reorder_queries", 2), "autotuned": tuned,
                    "seed": instance_seed(rank), "l2": "flushed between timed steps (256 MB write)",
                    "step": "rebuild of the index (keys+sort+decode) + learned-model fit if enabled + query batch"},
-        "roofline": {"kernel": "count_kernel", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "traffic": committed_traffic("count_kernel", alg_bytes),
-                     "algorithmic_bytes": alg_bytes, "avg_launch_ms": count_avg_ms},
+        "roofline": kern[dominant],
+        "roofline_other": [v for k, v in kern.items() if k != dominant],
         "gpu_launches": int(launches),
         "clocks": clk,
         "breakdown": {
