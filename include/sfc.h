@@ -314,7 +314,8 @@ sfc_status sfc_model_get(const sfc_index* idx, int* h_root, float* h_params, int
 sfc_status sfc_model_fence(const sfc_index* idx, uint64_t* h_fence, int* h_leaves, void* stream);
 
 /* Work of the last query batch: points scanned (sum over queries of the interval lengths,
- * the S_q of Alg. 1's scan loop), scan chunks, and points reported.  Synchronises. */
+ * the S_q of Alg. 1's scan loop), scan chunks (queries that scan at most 64 points have none:
+ * one thread scans each of them), and points reported.  Synchronises. */
 sfc_status sfc_query_stats(const sfc_index* idx, uint64_t* h_scanned, uint64_t* h_chunks,
                            uint64_t* h_hits, void* stream);
 

@@ -9,18 +9,22 @@
 //                  with abutting intervals merged, then lower_bound of both ends of every
 //                  interval, by binary search or by the learned model (fence bracket and
 //                  error window, verified, with fallback).  The query's scan length S_q is cut
-//                  into chunks of C points.  plan3_kernel does the same for 3-D points.
+//                  into chunks of C points; a query with S_q <= kSmallScan gets no chunks and
+//                  goes onto the small-query list instead.  plan3_kernel does the same for 3-D
+//                  points.
 //   scan           exclusive scan of the chunk counts -> chunk bases.
 //   count_kernel   persistent warps take batches of chunks from a counter (work stealing);
 //                  a warp streams the chunk's coordinates, applies the exact window test
 //                  (disc dx^2 + dy^2 <= delta^2 in int64, square, or 3-D ball), keeps the warp
 //                  ballots as a hit bitmask (one bit per scanned point) and adds the chunk's
-//                  popcount to the query's count.
+//                  popcount to the query's count.  Once the chunks are all claimed, the warps
+//                  take the listed small queries, one thread per query, with the same test.
 //   scan           exclusive scan of the per-query counts -> the caller's out_offsets.
 //   write_kernel   persistent warps take batches of queries; a warp walks its query's
 //                  chunks in order, reads the bitmask (or, past the bitmask budget, re-runs
 //                  the filter) and writes the ids of the hits with ballot/popc compaction at
-//                  out_offsets[q] + rank, so each query's ids come out in array order.
+//                  out_offsets[q] + rank, so each query's ids come out in array order; then
+//                  the small queries, one thread each, from their own masks.
 //
 // The bitmask makes the second pass read 1 bit instead of 8 bytes per scanned point.  In the
 // two scan passes a warp keeps its query's intervals (array shift and end of each, in the
