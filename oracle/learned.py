@@ -203,3 +203,74 @@ def fence_bracket(fence: np.ndarray, first: int, end: int, t: int, k: int = FENC
     lo = first if s == 0 else first + ((s - 1) * c) // k + 1
     hi = end if s == k else first + (s * c) // k
     return lo, hi
+
+
+# --------------------------------------------------------------------------------------
+# the query-time predict function, in the precision the queries use (fp32)
+# --------------------------------------------------------------------------------------
+# The error window of a leaf is an integer decided by fp32 arithmetic: the position predicted
+# for key k is first + floor(fma(slope, f32(k - base), icpt)) with every operation rounded to
+# nearest (ties to even) in IEEE single precision, the product and sum fused (one rounding).
+# The helpers below reproduce that rounding exactly from integer and fp64 arithmetic, so the
+# windows can be compared exactly; tests/test_oracle_learned.py pins them against exact
+# rational arithmetic.
+
+def _bit_length_u64(v: np.ndarray) -> np.ndarray:
+    v = np.asarray(v, np.uint64).copy()
+    bl = np.zeros(v.shape, np.int64)
+    for s in (32, 16, 8, 4, 2, 1):
+        big = v >= np.uint64(1 << s)
+        bl += s * big
+        v = np.where(big, v >> np.uint64(s), v)
+    return bl + (v > 0)
+
+
+def f32_of_int(v: np.ndarray) -> np.ndarray:
+    """int64 values rounded to the nearest float32 (ties to even), returned as float32."""
+    v = np.asarray(v, np.int64)
+    neg = v < 0
+    a = np.where(neg, -v, v).astype(np.uint64)          # |v| < 2^63
+    bl = _bit_length_u64(a)
+    shift = np.maximum(bl - 24, 0).astype(np.uint64)
+    q = a >> shift
+    rem = a - (q << shift)
+    half = np.where(shift > 0, np.uint64(1) << (np.maximum(shift, np.uint64(1)) - np.uint64(1)), np.uint64(0))
+    up = (shift > 0) & ((rem > half) | ((rem == half) & ((q & np.uint64(1)) == 1)))
+    q = q + up.astype(np.uint64)
+    mag = q.astype(np.float64) * np.exp2(shift.astype(np.float64))   # exact: q <= 2^24
+    return np.where(neg, -mag, mag).astype(np.float32)
+
+
+def fma_f32(a: np.ndarray, b: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """a * b + c for float32 inputs with a single rounding to float32 (ties to even).
+
+    a * b is exact in fp64 (two 24-bit significands); the fp64 sum s = a*b + c and its exact
+    error e come from the TwoSum algorithm (Knuth); s is then moved to round-to-odd (one ulp
+    towards e when e != 0 and s's last significand bit is 0), and the round-to-odd fp64 value,
+    having at least two more bits than float32, rounds to the correctly rounded float32
+    (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums", 2008)."""
+    a = np.asarray(a, np.float32).astype(np.float64)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    c = np.asarray(c, np.float32).astype(np.float64)
+    ab = a * b
+    s = ab + c
+    bb = s - ab
+    e = (ab - (s - bb)) + (c - bb)
+    s = np.atleast_1d(s).copy()
+    e = np.atleast_1d(e)
+    even = (s.view(np.int64) & 1) == 0
+    fix = (e != 0) & even
+    if fix.any():
+        s[fix] = np.nextafter(s[fix], np.where(e[fix] > 0, np.inf, -np.inf))
+    return s.astype(np.float32)
+
+
+def predict_positions(slope: float, icpt: float, first: int, base: int, keys: np.ndarray) -> np.ndarray:
+    """Predicted positions of keys routed to a leaf: first + floor(p), p = fma(slope,
+    f32(key - base), icpt) in float32, clamped to [-2e9, 2e9] (the difference taken as a
+    signed 64-bit integer)."""
+    d = (np.asarray(keys, np.uint64) - np.uint64(base)).view(np.int64)
+    u = f32_of_int(d)
+    p = fma_f32(np.full(u.shape, slope, np.float32), u, np.full(u.shape, icpt, np.float32))
+    p = np.minimum(np.maximum(p, np.float32(-2.0e9)), np.float32(2.0e9))
+    return int(first) + np.floor(p.astype(np.float64)).astype(np.int64)

@@ -96,7 +96,8 @@ def test_roads_3e7_graph_full(cuda):
 
 def test_mixed_1e8_learned_vs_binary_full(cuda):
     """10^8 points, 10^7 queries, Z order, 4096-leaf learned model: the learned-bounds output is
-    bit-identical to the binary-search output, and sampled queries match brute force."""
+    bit-identical to the binary-search output, 10^5 sampled queries equal the oracle's id lists
+    (in order) and 100 of them match brute force."""
     wl = W.mixed_1e8()
     pts, q, d = to_dev(wl.points, cuda), to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
     idx = sfc.sfc_build(pts, "z", bounds="learned", leaves=4096)
@@ -110,8 +111,17 @@ def test_mixed_1e8_learned_vs_binary_full(cuda):
     assert torch.equal(ids_b, ids_l)
     del ids_b
     assert stats["misses"] <= 0.001 * stats["endpoints"], stats
-    sample = np.random.default_rng(2).choice(wl.m, 100, replace=False)
-    check_sampled_queries(off_l, ids_l, wl.points, wl.queries, wl.delta, sample)
+    # exact id lists, in order, of 10^5 sampled queries against the oracle's Alg. 1 over the
+    # whole point set, and 100 of them by set against brute force
+    ref = oracle.build(wl.points, 30, "z")
+    sample = np.sort(np.random.default_rng(2).choice(wl.m, 100_000, replace=False))
+    roff, rids = oracle.query(ref, wl.queries[sample], wl.delta[sample], threads=THREADS)
+    o, out = u64(off_l), u32(ids_l)
+    got_len = (o[sample + 1] - o[sample]).astype(np.int64)
+    assert np.array_equal(got_len, np.diff(roff.astype(np.int64)))
+    got = np.concatenate([out[o[qi]:o[qi + 1]] for qi in sample])
+    assert np.array_equal(got, rids)
+    check_sampled_queries(off_l, ids_l, wl.points, wl.queries, wl.delta, sample[:100])
     assert sfc.sfc_device_status(idx) == (0, 0)
 
 

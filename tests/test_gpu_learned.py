@@ -193,3 +193,57 @@ def test_fence_matches_oracle(cuda, curve):
     assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
     st = sfc.sfc_model_stats(idx)
     assert st["misses"] == 0 and st["window_sum"] / st["endpoints"] < 0.5 * wl.n / 4096 + 2
+
+
+def _leaf_stage_points(kind):
+    if kind == "clustered":   # all clustered (the dynamic workload's base shape), n = 10^6
+        return W.dynamic_5e7(scale=0.02, rounds=1).base
+    return W.mixed_1e7(scale=0.1 if kind == "mixed-1e6" else 1.0).points
+
+
+@pytest.mark.parametrize("curve,root,kind", [("z", "pwl", "mixed-1e6"), ("h", "pwl", "mixed-1e6"),
+                                             ("z", "mlp", "mixed-1e6"), ("z", "pwl", "clustered"),
+                                             ("z", "pwl", "mixed-1e7")])
+def test_leaf_stage_matches_oracle(cuda, curve, root, kind):
+    """The leaf stage of the fit against the oracle, leaf by leaf over the oracle's sorted keys.
+
+    Line: the GPU's least-squares line of position against key offset (fitted in fp32) equals
+    oracle.learned.leaf_fit (fp64 normal equations): slope within a relative 1e-3, and the two
+    lines within 1e-3 * (keys in the leaf) + 1e-3 positions of each other at both ends of the
+    leaf's key range (fp32 sums over up to a few 10^4 keys lose about 1e-5 relative; a wrong
+    term or sign is off by whole positions).
+    Error window: err_lo and err_hi are exactly the min and max of position - prediction over
+    the leaf's keys, with the prediction taken by the query-time fp32 function
+    (oracle.learned.predict_positions) from the leaf's own slope and intercept -- so every key
+    of every leaf lies in its window and both ends are attained; empty leaves get (0, 0)."""
+    pts = _leaf_stage_points(kind)
+    idx = sfc.sfc_build(to_dev(pts, cuda), curve, bounds="learned", root=root)
+    m = sfc.sfc_model_get(idx)
+    keys = oracle.build(pts, 30, curve).keys
+    n = keys.shape[0]
+    first, end = m["first"].astype(np.int64), m["end"].astype(np.int64)
+    assert first[0] == 0 and end[-1] == n and np.all(end >= first)
+    L = first.shape[0]
+    checked = 0
+    for j in range(L):
+        f, e = int(first[j]), int(end[j])
+        c = e - f
+        if c == 0:
+            assert m["err_lo"][j] == 0 and m["err_hi"][j] == 0, j
+            continue
+        kk = keys[f:e]
+        base = int(kk[0])
+        u = (kk - np.uint64(base)).astype(np.float64)
+        s_ref, c_ref = OL.leaf_fit(u, np.arange(c, dtype=np.float64))
+        s_gpu, c_gpu = float(m["slope"][j]), float(m["icpt"][j])
+        if c >= 2:
+            assert abs(s_gpu - s_ref) <= 1e-3 * abs(s_ref) + 1e-30, (j, s_gpu, s_ref)
+            for uu in (0.0, float(u[-1])):
+                assert abs((s_gpu * uu + c_gpu) - (s_ref * uu + c_ref)) <= 1e-3 * c + 1e-3, (j, uu)
+        pred = OL.predict_positions(m["slope"][j], m["icpt"][j], f, base, kk)
+        res = np.clip(np.arange(f, e, dtype=np.int64) - pred, -0x7fffffff, 0x7fffffff)
+        assert int(m["err_lo"][j]) == int(res.min()) and int(m["err_hi"][j]) == int(res.max()), \
+            (j, int(m["err_lo"][j]), int(m["err_hi"][j]), int(res.min()), int(res.max()))
+        checked += 1
+    assert checked > 0.9 * L
+    idx.close()

@@ -52,4 +52,5 @@ def test_two_ranks_gloo():
 
 def test_single_rank_is_local_time():
     assert bench.max_over_ranks(12.5, None) == 12.5
-    assert bench.instance_seed(0) == 2                   # rank 0 answers the canonical mixed-1e7 seed
+    assert bench.instance_seed(0) == 4                   # rank 0 answers the canonical mixed-1e8 seed
+    assert bench.instance_seed(0, "mixed-1e7") == 2

@@ -128,3 +128,23 @@ def test_refined_drop0_is_subset_of_cells():
         full, _ = oracle.cells(qx, qy, delta)
         sub = oracle.cells_refined(qx, qy, delta, drop=0)
         assert set(sub) <= set(full) and len(sub) >= 1
+
+
+@pytest.mark.parametrize("intervals,merged", [
+    ([], []),                                                     # no interval
+    ([(5, 9)], [(5, 9)]),                                         # single
+    ([(0, 3), (4, 7)], [(0, 7)]),                                 # abutting: 3 + 1 == 4
+    ([(0, 3), (5, 7)], [(0, 3), (5, 7)]),                         # one key apart: kept apart
+    ([(0, 3), (4, 7), (8, 8), (10, 12), (13, 15)], [(0, 8), (10, 15)]),   # chains and a gap
+    ([(16, 31), (32, 47), (64, 79), (80, 95)], [(16, 47), (64, 95)]),     # aligned cells of 16 keys
+    ([(2 ** 60 - 8, 2 ** 60 - 5), (2 ** 60 - 4, 2 ** 60 - 1)], [(2 ** 60 - 8, 2 ** 60 - 1)]),   # top of the key space
+    ([(0, 0), (1, 1), (2, 2), (3, 3)], [(0, 3)]),                 # cells of one key (level 0)
+])
+def test_merge_abutting_table(intervals, merged):
+    """Intervals sorted by lo and pairwise disjoint (as the cells of a cover are): those whose
+    end is followed by the next one's start are joined, the others kept; the keys covered
+    are unchanged."""
+    assert oracle.merge_abutting(intervals) == merged
+    keys = lambda iv: [k for a, z in iv for k in range(a, z + 1)] if all(z - a < 64 for a, z in iv) else None
+    if keys(intervals) is not None and keys(merged) is not None:
+        assert keys(merged) == keys(intervals)

@@ -130,3 +130,79 @@ def test_fence_bracket_holds_lower_bound():
             assert hi - lo <= (end - first) // L.FENCE + 1
     e = L.leaf_fence(keys, 5, 5)
     assert np.all(e == np.iinfo(np.uint64).max)
+
+
+# --------------------------------------------------------------------------------------
+# the fp32 predict function (error windows are integers decided in fp32)
+# --------------------------------------------------------------------------------------
+
+def _round_f32_exact(x):
+    """Nearest float32 (ties to even) of a rational x in the normal range, by integer
+    arithmetic on the exact value: scale to a 24-bit significand and round the integer."""
+    from fractions import Fraction
+    x = Fraction(x)
+    if x == 0:
+        return 0.0
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    assert Fraction(2) ** e <= a < Fraction(2) ** (e + 1)
+    m = a / Fraction(2) ** (e - 23)                 # in [2^23, 2^24)
+    q, r = divmod(m.numerator, m.denominator)
+    rr = Fraction(r, m.denominator)
+    if rr > Fraction(1, 2) or (rr == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    return sign * float(Fraction(q) * Fraction(2) ** (e - 23))
+
+
+def test_f32_of_int_rounds_to_nearest_even():
+    rng = np.random.default_rng(7)
+    vals = [0, 1, -1, 2 ** 24, 2 ** 24 + 1, 2 ** 24 + 3, 2 ** 25 + 2, 2 ** 25 + 6, 2 ** 53 + 1,
+            2 ** 60 - 1, -(2 ** 59 + 2 ** 35), (1 << 62) + (1 << 38)]
+    vals += [int(v) for v in rng.integers(-(2 ** 62), 2 ** 62, 3000)]
+    vals += [int(v) >> int(s) for v, s in zip(rng.integers(0, 2 ** 62, 3000), rng.integers(0, 62, 3000))]
+    got = L.f32_of_int(np.array(vals, np.int64))
+    want = np.array([_round_f32_exact(v) for v in vals], np.float64)
+    assert np.array_equal(got.astype(np.float64), want)
+
+
+def test_fma_f32_is_correctly_rounded():
+    """fused a*b + c with one rounding, against exact rational arithmetic; includes products
+    whose sum with c lands exactly half-way between two floats and cancellations."""
+    from fractions import Fraction
+    rng = np.random.default_rng(8)
+    a = rng.normal(0, 1, 4000).astype(np.float32) * np.float32(2.0) ** rng.integers(-40, 0, 4000).astype(np.float32)
+    b = L.f32_of_int(rng.integers(0, 2 ** 50, 4000))
+    c = (rng.normal(0, 1, 4000) * 10.0 ** rng.integers(-2, 6, 4000)).astype(np.float32)
+    # exact ties: a*b = 2^-24 is half an ulp of c in [1, 2) -> ties to even
+    a[:40] = np.float32(1.0)
+    b[:40] = np.float32(2.0 ** -24)
+    c[:40] = np.where(np.arange(40) % 2 == 0, np.float32(1.0), np.float32(1.0 + 2.0 ** -23))
+    # just below a tie: a*b = 2^-24 - k^2 2^-70 with c = 1 + 2^-23 (odd); the fp64 sum rounds
+    # onto the tie itself, so rounding that to float32 would go up, while the exact value rounds
+    # down
+    k = np.arange(1, 41, dtype=np.float64)
+    a[40:80] = (1.0 + k * 2.0 ** -23).astype(np.float32)
+    b[40:80] = ((1.0 - k * 2.0 ** -23) * 2.0 ** -24).astype(np.float32)
+    c[40:80] = np.float32(1.0 + 2.0 ** -23)
+    naive = (a[40:80].astype(np.float64) * b[40:80].astype(np.float64) + c[40:80].astype(np.float64)).astype(np.float32)
+    assert np.all(naive == np.float32(1.0 + 2.0 ** -22))   # the double rounding this must avoid
+    # cancellation
+    c[100:150] = -(a[100:150].astype(np.float64) * b[100:150].astype(np.float64)).astype(np.float32)
+    got = L.fma_f32(a, b, c)
+    want = [_round_f32_exact(Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z)))
+            for x, y, z in zip(a, b, c)]
+    assert np.array_equal(got.astype(np.float64), np.array(want, np.float64))
+
+
+def test_predict_positions_small_case():
+    """slope 0.5, icpt 1.25: key offsets 0, 1, 2, 3, 5 -> floor(1.25, 1.75, 2.25, 2.75, 3.75)."""
+    keys = np.array([100, 101, 102, 103, 105], np.uint64)
+    p = L.predict_positions(0.5, 1.25, 10, 100, keys)
+    assert p.tolist() == [11, 11, 12, 12, 13]
+    # keys below the base give negative offsets (signed difference)
+    assert L.predict_positions(1.0, 0.0, 10, 100, np.array([98], np.uint64)).tolist() == [8]
+    # the prediction is clamped to [-2e9, 2e9] before the floor
+    assert L.predict_positions(1e30, 0.0, 0, 0, np.array([5], np.uint64)).tolist() == [2_000_000_000]
