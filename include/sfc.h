@@ -371,7 +371,10 @@ sfc_status sfc_decode(const uint64_t* d_keys, uint64_t n, sfc_curve curve, int32
 sfc_status sfc_sort_pairs(const uint64_t* d_keys_in, const uint32_t* d_ids_in, uint64_t n,
                           uint64_t* d_keys_out, uint32_t* d_ids_out, void* stream);
 
-/* Exclusive prefix sum of n uint32 into uint64[n+1] (the last entry is the total). */
+/* Exclusive prefix sum of n uint32 into uint64[n+1] (the last entry is the total), with the
+ * library's single-pass decoupled look-back scan.  Allocates and frees its own workspace on
+ * `stream` and synchronises `stream`: returns SFC_ERR_TIMEOUT (output void) if a look-back
+ * wait gave up. */
 sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
 
 /* sfc_exclusive_scan without any device allocation.  No counterpart in the paper: this is
@@ -379,16 +382,26 @@ sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out,
  * owned by a caching pool of a host framework (an allocation from inside this library would
  * go around the pool and can fail once the pool holds the memory), or a latency-bound loop
  * that cannot take the implicit device synchronisation of cudaMalloc/cudaFree.  The call
- * only enqueues a memset and one kernel on `stream`.
+ * only enqueues a memset and one kernel on `stream` and does not synchronise.
  * Scratch: a fixed 131 KB array in device memory of every device that loads the library,
  * held until the process exits; n may be at most 67,108,864 (16,384 tiles of 4,096),
  * larger n returns SFC_ERR_CAPACITY and enqueues nothing.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current, so make
- * that first call before capturing a stream into a CUDA graph.  All calls share the one
- * array (it keeps the last call's words; each call clears what it uses first), so calls that
- * can overlap on the GPU -- on different streams, or different host threads -- race and must
- * be serialised by the caller.  Output: d_out uint64[n+1] as sfc_exclusive_scan. */
+ * that first call before capturing a stream into a CUDA graph; the address is looked up
+ * again when the device's CUDA context was destroyed and created again (cudaDeviceReset).
+ * All calls share the one array (it keeps the last call's words; each call clears what it
+ * uses first), so calls that can overlap on the GPU -- on different streams, or different
+ * host threads -- race and must be serialised by the caller.  Output: d_out uint64[n+1] as
+ * sfc_exclusive_scan.  A look-back wait that gave up is recorded in the array's status word,
+ * read by sfc_exclusive_scan_noalloc_status. */
 sfc_status sfc_exclusive_scan_noalloc(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream);
+
+/* Status of the most recent sfc_exclusive_scan_noalloc on the current device: synchronises
+ * `stream` (the stream of that call, or one ordered after it), writes the status bits
+ * (SFC_DEV_TIMEOUT if a look-back wait gave up and the output is void) to *h_bits (may be
+ * NULL) and returns SFC_ERR_TIMEOUT in that case, else SFC_OK.  Allocates nothing; it reads
+ * the shared array, so the same serialisation applies as to the scan itself. */
+sfc_status sfc_exclusive_scan_noalloc_status(uint32_t* h_bits, void* stream);
 
 /* Ranges and bounds of a query batch (Alg. 1, range derivation and bound search): for each
  * query i, the merged key intervals of its cover -- cells(Q), or the finer cover set by

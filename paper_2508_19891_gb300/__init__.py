@@ -113,6 +113,7 @@ def lib():
             "sfc_sort_pairs": (ci, [P, P, u64, P, P, P]),
             "sfc_exclusive_scan": (ci, [P, u64, P, P]),
             "sfc_exclusive_scan_noalloc": (ci, [P, u64, P, P]),
+            "sfc_exclusive_scan_noalloc_status": (ci, [P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
             "sfc_autotune": (ci, [P, P, P, u64, ci, P, P, P, P]),
@@ -636,13 +637,33 @@ def sfc_exclusive_scan(x: torch.Tensor, stream=None):
 
 def sfc_exclusive_scan_noalloc(x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """Exclusive scan through the entry point that allocates no device memory (the output
-    buffer, if not given, is allocated here by torch, outside the library call)."""
+    buffer, if not given, is allocated here by torch, outside the library call).  x: 32-bit
+    integers (read as uint32); out: int64, contiguous, on x's device, at least n + 1 long."""
+    if x.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise ValueError(f"x must hold 32-bit integers, not {x.dtype}")
     x = x.contiguous()
     if out is None:
         out = torch.empty(x.numel() + 1, dtype=torch.int64, device=x.device)
+    if out.dtype != torch.int64:
+        raise ValueError(f"out must be int64, not {out.dtype}")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if out.device != x.device or not x.is_cuda:
+        raise ValueError(f"x and out must be on the same CUDA device ({x.device}, {out.device})")
+    if out.numel() < x.numel() + 1:
+        raise ValueError(f"out holds {out.numel()} elements; the scan of {x.numel()} writes {x.numel() + 1}")
     _check(lib().sfc_exclusive_scan_noalloc(_dptr(x), x.numel(), _dptr(out), _stream(stream)),
            "sfc_exclusive_scan_noalloc")
     return out
+
+
+def sfc_exclusive_scan_noalloc_status(stream=None) -> int:
+    """Status bits of the most recent no-allocation scan on the current device (synchronises
+    the stream); raises SfcError(SFC_ERR_TIMEOUT) if a look-back wait gave up."""
+    bits = ctypes.c_uint32(0)
+    _check(lib().sfc_exclusive_scan_noalloc_status(ctypes.byref(bits), _stream(stream)),
+           "sfc_exclusive_scan_noalloc_status")
+    return int(bits.value)
 
 
 def sfc_query_ranges(index: Index, q: torch.Tensor, delta: torch.Tensor, stream=None):

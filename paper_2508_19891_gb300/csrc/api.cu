@@ -1048,11 +1048,7 @@ sfc_status sfc_sort_pairs(const uint64_t* d_keys_in, const uint32_t* d_ids_in, u
 sfc_status sfc_exclusive_scan(const uint32_t* d_in, uint64_t n, uint64_t* d_out, void* stream)
 {
     if (!d_out || (n && !d_in)) return SFC_ERR_INVALID;
-    cudaStream_t st = as_stream(stream);
-    ScanWorkspace ws;
-    sfc_status s = exclusive_scan_u32(d_in, n, d_out, ws, nullptr, st);
-    ws.flags.release(st);
-    return s;
+    return exclusive_scan_standalone(d_in, n, d_out, as_stream(stream));
 }
 
 sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,

@@ -8,6 +8,8 @@
 // its own inclusive prefix and writes its outputs.  A word packs a 2-bit flag with a
 // 62-bit sum.  The wait on a predecessor is bounded: past kSpinLimit reads it sets
 // SFC_DEV_TIMEOUT and continues with the partial sum.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "sfc_internal.cuh"
@@ -152,40 +154,112 @@ sfc_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, Sca
     return launch_status();
 }
 
+// The standalone scan (sfc_exclusive_scan): its own workspace with a status word in front
+// (word 0 status, word 1 tile counter, then the tiles' words), read back once the kernel is
+// done so that a look-back wait that gave up is reported by the call itself.
+sfc_status exclusive_scan_standalone(const uint32_t* in, uint64_t n, uint64_t* out, cudaStream_t st)
+{
+    if (n == 0) {
+        SFC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+        return SFC_OK;
+    }
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    if (tiles > 0x7fffffffull) return SFC_ERR_INVALID;
+    DevBuf ws;
+    SFC_TRY(ws.ensure((tiles + 2) * sizeof(uint64_t), st));
+    uint64_t* words = ws.as<uint64_t>();
+    sfc_status s = SFC_OK;
+    uint32_t bits = 0;
+    if (cudaMemsetAsync(words, 0, (tiles + 2) * sizeof(uint64_t), st) != cudaSuccess) s = SFC_ERR_CUDA;
+    if (s == SFC_OK) {
+        const int vec = ((((uintptr_t)in) & 15) == 0) && ((((uintptr_t)out) & 15) == 0);
+        scan_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(in, n, out, words + 1, reinterpret_cast<uint32_t*>(words),
+                                                          vec);
+        count_launch();
+        s = launch_status();
+    }
+    if (s == SFC_OK && cudaMemcpyAsync(&bits, words, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = SFC_ERR_CUDA;
+    ws.release(st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && s == SFC_OK) s = SFC_ERR_CUDA;
+    if (s == SFC_OK && (bits & SFC_DEV_TIMEOUT)) s = SFC_ERR_TIMEOUT;
+    return s;
+}
+
 // ------------------------------------------------------------------------------------
 // Scan without allocation (sfc_exclusive_scan_noalloc).
 //
-// For callers that must not allocate device memory.  Its look-back words live in a
-// file-scope device array of fixed size instead of a cudaMallocAsync buffer; host code
-// cannot use the array's name as a device address (it is a host-side stand-in), so the
-// address is taken once per device with cudaGetSymbolAddress while that device is current.
+// For callers that must not allocate device memory.  Its scratch lives in a file-scope
+// device array of fixed size instead of a cudaMallocAsync buffer: word 0 is a status word
+// (SFC_DEV_TIMEOUT when a look-back wait of the last call gave up), word 1 the tile counter,
+// words 2 .. 2 + tiles the tiles' look-back words.  Host code cannot use the array's name as a
+// device address (it is a host-side stand-in), so the address is looked up with
+// cudaGetSymbolAddress while the device is current, once per device and CUDA context: a
+// context that was torn down and created again (cudaDeviceReset) gets a new id, and the
+// address is looked up again for it.
 // ------------------------------------------------------------------------------------
 constexpr uint64_t kNoAllocMaxTiles = 16384;                       // 131 KB of words
 constexpr uint64_t kNoAllocMaxItems = kNoAllocMaxTiles * kTile;     // 67,108,864 elements
-static __device__ __align__(256) uint64_t g_noalloc_scan_words[kNoAllocMaxTiles + 1];
+static __device__ __align__(256) uint64_t g_noalloc_scan_words[kNoAllocMaxTiles + 2];
 
 namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-uint64_t* g_noalloc_words[kMaxDevices] = {};
+struct NoAllocSlot {
+    uint64_t* words = nullptr;
+    unsigned long long ctx_id = 0;   // id of the context the address belongs to (0: unknown)
+};
+NoAllocSlot g_noalloc[kMaxDevices];
 
-// Device address of the array for the current device (looked up on first use).
+// Id of the calling thread's current CUDA context (ids are never reused within a process);
+// false if it cannot be had.  The two driver calls are reached through the runtime's
+// entry-point lookup, so the library does not link the driver library itself.
+bool current_context_id(unsigned long long* id)
+{
+    using GetCurrentFn = CUresult (*)(CUcontext*);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // under g_noalloc_mu
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
+                                             cudaEnableDefault, &q1) != cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000,
+                                             cudaEnableDefault, &q2) != cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the array for the current device and context (looked up on first use).
 sfc_status noalloc_words(uint64_t** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SFC_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_words[dev]) {
+    NoAllocSlot& slot = g_noalloc[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (!slot.words || (have_id && id != slot.ctx_id)) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scan_words);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return SFC_ERR_CUDA;
         }
-        g_noalloc_words[dev] = static_cast<uint64_t*>(p);
+        slot.words = static_cast<uint64_t*>(p);
+        // the lookup created the context if there was none yet
+        slot.ctx_id = (have_id || current_context_id(&id)) ? id : 0;
     }
-    *out = g_noalloc_words[dev];
+    *out = slot.words;
     return SFC_OK;
 }
 
@@ -201,15 +275,29 @@ extern "C" sfc_status sfc_exclusive_scan_noalloc(const uint32_t* d_in, uint64_t 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint64_t* words = nullptr;
     SFC_TRY(noalloc_words(&words));
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    // the status word, the tile counter and the look-back words of this call start at zero
+    SFC_CUDA_TRY(cudaMemsetAsync(words, 0, (tiles + 2) * sizeof(uint64_t), st));
     if (n == 0) {
         SFC_CUDA_TRY(cudaMemsetAsync(d_out, 0, sizeof(uint64_t), st));
         return SFC_OK;
     }
-    const uint64_t tiles = (n + kTile - 1) / kTile;
-    // the tile counter and the look-back words of this call must start at zero
-    SFC_CUDA_TRY(cudaMemsetAsync(words, 0, (tiles + 1) * sizeof(uint64_t), st));
     const int vec = ((((uintptr_t)d_in) & 15) == 0) && ((((uintptr_t)d_out) & 15) == 0);
-    scan_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(d_in, n, d_out, words, nullptr, vec);
+    scan_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(d_in, n, d_out, words + 1, reinterpret_cast<uint32_t*>(words),
+                                                      vec);
     count_launch();
     return launch_status();
+}
+
+extern "C" sfc_status sfc_exclusive_scan_noalloc_status(uint32_t* h_bits, void* stream)
+{
+    using namespace sfc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t* words = nullptr;
+    SFC_TRY(noalloc_words(&words));
+    uint32_t bits = 0;
+    SFC_CUDA_TRY(cudaMemcpyAsync(&bits, words, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_bits) *h_bits = bits;
+    return (bits & SFC_DEV_TIMEOUT) ? SFC_ERR_TIMEOUT : SFC_OK;
 }

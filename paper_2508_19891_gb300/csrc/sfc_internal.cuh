@@ -396,6 +396,9 @@ struct ScanWorkspace {
 sfc_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, ScanWorkspace& ws,
                               uint32_t* status, cudaStream_t st);
 sfc_status reserve_scan(ScanWorkspace& ws, uint64_t n, cudaStream_t st);
+// the same with its own workspace and status word; synchronises st and returns
+// SFC_ERR_TIMEOUT if a look-back wait gave up
+sfc_status exclusive_scan_standalone(const uint32_t* in, uint64_t n, uint64_t* out, cudaStream_t st);
 
 // radix.cu: the build sort.
 struct SortWorkspace {

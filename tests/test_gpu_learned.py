@@ -215,7 +215,9 @@ def test_leaf_stage_matches_oracle(cuda, curve, root, kind):
     Error window: err_lo and err_hi are exactly the min and max of position - prediction over
     the leaf's keys, with the prediction taken by the query-time fp32 function
     (oracle.learned.predict_positions) from the leaf's own slope and intercept -- so every key
-    of every leaf lies in its window and both ends are attained; empty leaves get (0, 0)."""
+    of every leaf lies in its window and both ends are attained; empty leaves get (0, 0).  (On
+    all-clustered points most of the 4,096 leaves stay empty: the 256-knot root cannot resolve
+    1,000 narrow clusters, so a few hundred leaves hold all keys.)"""
     pts = _leaf_stage_points(kind)
     idx = sfc.sfc_build(to_dev(pts, cuda), curve, bounds="learned", root=root)
     m = sfc.sfc_model_get(idx)
@@ -244,6 +246,6 @@ def test_leaf_stage_matches_oracle(cuda, curve, root, kind):
         res = np.clip(np.arange(f, e, dtype=np.int64) - pred, -0x7fffffff, 0x7fffffff)
         assert int(m["err_lo"][j]) == int(res.min()) and int(m["err_hi"][j]) == int(res.max()), \
             (j, int(m["err_lo"][j]), int(m["err_hi"][j]), int(res.min()), int(res.max()))
-        checked += 1
-    assert checked > 0.9 * L
+        checked += c
+    assert checked == n   # every key of every leaf was checked
     idx.close()
