@@ -69,6 +69,28 @@ typedef enum { SFC_NORM_DISC = 0, SFC_NORM_SQUARE = 1 } sfc_norm;
 
 typedef struct sfc_index sfc_index;   /* opaque; owned by the library */
 
+/* Device memory of an index from the caller's allocator instead of the library's.  With an
+ * allocator given at build, every device buffer of that index -- the sorted arrays, the
+ * learned model, the query and update workspaces, the staging buffers of the host-buffer
+ * calls -- is requested from alloc(bytes, stream, ctx) and returned with free(ptr, stream,
+ * ctx), both on the stream of the call that needs or drops the buffer (a cudaStream_t;
+ * stream-ordered like cudaMallocAsync / cudaFreeAsync: the memory may be used by work
+ * enqueued on that stream after alloc returns, and free may hand it to later work on that
+ * stream).  alloc returns a device pointer on the index's device, aligned to at least 256
+ * bytes, or NULL when it has no memory (the call then returns SFC_ERR_OOM).  The callbacks
+ * run on the thread of the library call, never concurrently for one index, and not while a
+ * stream is being captured once sfc_reserve has sized the index.  The struct is copied at
+ * build; ctx must stay valid until sfc_destroy returns.  This lets a framework's caching
+ * allocator (e.g. PyTorch's) own all of the index's memory.  A NULL allocator keeps the
+ * library's own stream-ordered pool (cudaMallocAsync on the device's default pool).  Calls
+ * that take no index (sfc_sort_pairs, sfc_exclusive_scan, the model-step calls) use the
+ * pool. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} sfc_allocator;
+
 typedef struct {
     sfc_bounds bounds;      /* bound search used by queries (default SFC_BOUNDS_BINARY) */
     int leaves;             /* learned model: number of leaf segments (default 4096) */
@@ -110,16 +132,18 @@ void sfc_default_options(sfc_options* opt);
 /* Builds an index over n points d_points (int32[n][2], device).  Keys of `curve`, then a
  * stable LSD radix sort of (key, id); the sorted coordinates are written alongside.
  * If opt->bounds is SFC_BOUNDS_LEARNED the learned model is trained as well.
- * n may be 0; n must be < 2^32 - 1.  *out receives the new index (NULL on error).
- * Errors: SFC_ERR_INVALID (NULL out, n too large, unknown curve), SFC_ERR_OOM,
- * SFC_ERR_CUDA.  Bad coordinates set SFC_DEV_BAD_POINT (keys of such points are
- * unspecified). */
+ * n may be 0; n must be < 2^32 - 1.  opt NULL = the defaults.  alloc: the allocator of all
+ * the index's device memory (see sfc_allocator), NULL = the library's pool.  *out receives
+ * the new index (NULL on error).  Errors: SFC_ERR_INVALID (NULL out, n too large, unknown
+ * curve, an allocator without both callbacks), SFC_ERR_OOM, SFC_ERR_CUDA.  Bad coordinates
+ * set SFC_DEV_BAD_POINT (keys of such points are unspecified). */
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
-                     const sfc_options* opt, void* stream);
+                     const sfc_options* opt, const sfc_allocator* alloc, void* stream);
 
-/* As sfc_build with the points in host memory (copied inside the call). */
+/* As sfc_build with the points in host memory (copied inside the call, into device memory
+ * from the same allocator). */
 sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, sfc_curve curve,
-                          const sfc_options* opt, void* stream);
+                          const sfc_options* opt, const sfc_allocator* alloc, void* stream);
 
 /* 3-D index (the paper's d-dimensional Z curve, Sec. 2.1, for d = 3): d_points int32[n][3]
  * with every coordinate in [0, 2^21); 63-bit keys (bit 3i = x_i, 3i + 1 = y_i, 3i + 2 = z_i);
@@ -133,17 +157,18 @@ sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, 
  * sfc_update, sfc_train_model, a learned bound search, cover 2 and square windows return
  * SFC_ERR_INVALID on it; queries run in input order. */
 sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt,
-                      void* stream);
+                      const sfc_allocator* alloc, void* stream);
 
 /* As sfc_build3 with the points in host memory (copied inside the call). */
 sfc_status sfc_build3_host(sfc_index** out, const int32_t* h_points, uint64_t n, const sfc_options* opt,
-                           void* stream);
+                           const sfc_allocator* alloc, void* stream);
 
 /* 2 for indexes made by sfc_build / sfc_build_host, 3 for sfc_build3 / sfc_build3_host; 0 for
  * NULL. */
 int sfc_index_dim(const sfc_index* idx);
 
-/* Frees the index and everything it owns (stream-ordered on the stream of the last call). */
+/* Frees the index and everything it owns (stream-ordered on the stream of the last call;
+ * memory from a caller's allocator goes back through its free callback). */
 void sfc_destroy(sfc_index* idx);
 
 /* Rebuilds the index in place over n new points (device), with the index's curve and
@@ -280,8 +305,9 @@ sfc_status sfc_train_model(sfc_index* idx, void* stream);
  * b[H], c; f(x) = c + sum_k exp(alpha_k) sigmoid(exp(beta_k) x + b_k)). */
 int sfc_model_hidden(void);
 
-/* Number of parameters of a root kind: MLP 3H + 1; piecewise linear K + 1 = 257
- * (d[K] log-increments then c; knot heights h_0 = c, h_{k+1} = h_k + exp(d_k)); -1 if unknown. */
+/* Number of parameters of a root kind: MLP 3H + 1; piecewise linear K + 1 = 257, the knot
+ * heights h_0 .. h_K of f(x) at x = k / K (kept non-decreasing: after every Adam step each
+ * height is raised to the running maximum of those before it); -1 if unknown. */
 int sfc_model_params(sfc_root root);
 
 /* Mean-squared error of the root on samples (x = key / 2^60, target y) and its gradient, from
@@ -306,12 +332,19 @@ sfc_status sfc_model_get(const sfc_index* idx, int* h_root, float* h_params, int
                          uint32_t* h_first, uint32_t* h_end, float* h_slope, float* h_icpt,
                          int32_t* h_err_lo, int32_t* h_err_hi, void* stream);
 
-/* Copies the leaves' fences out (host): uint64[*h_leaves][16], fence s of leaf j = the key at
- * position first_j + floor(s * (end_j - first_j) / 16) of the sorted array (all bits set for a
- * leaf without keys).  A learned search brackets its target between two fence keys before
- * the last-mile search.  h_fence must hold leaves * 16 entries.  SFC_ERR_STATE if no model.
- * Synchronises. */
+/* Copies the leaves' coarse fences out (host): uint64[*h_leaves][16], fence s of leaf j = the
+ * key at position first_j + floor(s * (end_j - first_j) / 16) of the sorted array (all bits
+ * set for a leaf without keys).  h_fence must hold leaves * 16 entries.  SFC_ERR_STATE if no
+ * model.  Synchronises. */
 sfc_status sfc_model_fence(const sfc_index* idx, uint64_t* h_fence, int* h_leaves, void* stream);
+
+/* Copies the leaves' fine fences out (host): uint64[*h_leaves][256], fine fence key r of leaf j
+ * = the key at position first_j + floor(r * (end_j - first_j) / 256) (all bits set for a leaf
+ * without keys); coarse fence key s is fine fence key 16 s.  A learned search counts the fine
+ * keys inside its error window that lie below the target, which brackets it between two fine
+ * keys before the last-mile search.  h_fence must hold leaves * 256 entries.  SFC_ERR_STATE if
+ * no model.  Synchronises. */
+sfc_status sfc_model_fence_fine(const sfc_index* idx, uint64_t* h_fence, int* h_leaves, void* stream);
 
 /* Work of the last query batch: points scanned (sum over queries of the interval lengths,
  * the S_q of Alg. 1's scan loop), scan chunks (queries that scan at most 64 points have none:
@@ -431,6 +464,10 @@ sfc_status sfc_profile_read(sfc_index* idx, sfc_profile_entry* out, int max, int
 
 /* Number of this library's kernels launched by this process so far (host counter). */
 uint64_t sfc_launch_count(void);
+
+/* Device bytes this process's calls currently hold from the library's own stream-ordered
+ * pool (host counter; memory from a caller's sfc_allocator is not counted). */
+uint64_t sfc_pool_bytes_in_use(void);
 
 /* Human-readable name of a status code. */
 const char* sfc_status_string(sfc_status s);

@@ -53,6 +53,51 @@ class sfc_options(ctypes.Structure):
                 ("query_norm", ctypes.c_int)]
 
 
+SFC_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+SFC_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class sfc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", SFC_ALLOC_FN), ("free", SFC_FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """sfc_allocator callbacks backed by PyTorch's CUDA caching allocator, so that torch owns
+    all of an index's device memory (torch.cuda.memory_allocated() counts it).  Keeps a
+    record of the blocks handed out (address -> bytes) and of every request and release."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.live = {}
+        self.allocs = 0
+        self.frees = 0
+        self.bytes_requested = 0
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device.index, int(stream or 0))
+            except Exception:
+                return None
+            self.live[int(p)] = int(nbytes)
+            self.allocs += 1
+            self.bytes_requested += int(nbytes)
+            return int(p)
+
+        def _free(ptr, stream, ctx):
+            self.live.pop(int(ptr), None)
+            self.frees += 1
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        # the ctypes function objects must outlive every index built with this allocator
+        self._alloc = SFC_ALLOC_FN(_alloc)
+        self._free = SFC_FREE_FN(_free)
+        self.struct = sfc_allocator(self._alloc, self._free, None)
+
+    def owns(self, ptr: int, nbytes: int = 1) -> bool:
+        """Whether [ptr, ptr + nbytes) lies inside a block handed out and not yet returned."""
+        return any(a <= ptr and ptr + nbytes <= a + b for a, b in self.live.items())
+
+
 class sfc_profile_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
@@ -78,8 +123,8 @@ def lib():
         PP = ctypes.POINTER(ctypes.c_void_p)
         sig = {
             "sfc_default_options": (None, [ctypes.POINTER(sfc_options)]),
-            "sfc_build": (ci, [PP, P, u64, ci, ctypes.POINTER(sfc_options), P]),
-            "sfc_build_host": (ci, [PP, P, u64, ci, ctypes.POINTER(sfc_options), P]),
+            "sfc_build": (ci, [PP, P, u64, ci, ctypes.POINTER(sfc_options), ctypes.POINTER(sfc_allocator), P]),
+            "sfc_build_host": (ci, [PP, P, u64, ci, ctypes.POINTER(sfc_options), ctypes.POINTER(sfc_allocator), P]),
             "sfc_destroy": (None, [P]),
             "sfc_query_count": (ci, [P, P, P, u64, P, P]),
             "sfc_query_write": (ci, [P, P, P, u64, P, P, u64, P]),
@@ -89,8 +134,9 @@ def lib():
             "sfc_set_bounds_mode": (ci, [P, ci]),
             "sfc_set_cover": (ci, [P, ci]),
             "sfc_model_fence": (ci, [P, P, P, P]),
-            "sfc_build3": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
-            "sfc_build3_host": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), P]),
+            "sfc_model_fence_fine": (ci, [P, P, P, P]),
+            "sfc_build3": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), ctypes.POINTER(sfc_allocator), P]),
+            "sfc_build3_host": (ci, [PP, P, u64, ctypes.POINTER(sfc_options), ctypes.POINTER(sfc_allocator), P]),
             "sfc_index_dim": (ci, [P]),
             "sfc_keys3": (ci, [P, u64, P, P]),
             "sfc_set_query_norm": (ci, [P, ci]),
@@ -116,6 +162,7 @@ def lib():
             "sfc_exclusive_scan_noalloc_status": (ci, [P, P]),
             "sfc_query_ranges": (ci, [P, P, P, u64, P, P, P, P, P, P]),
             "sfc_launch_count": (u64, []),
+            "sfc_pool_bytes_in_use": (u64, []),
             "sfc_autotune": (ci, [P, P, P, u64, ci, P, P, P, P]),
             "sfc_rebuild": (ci, [P, P, u64, P]),
             "sfc_reserve": (ci, [P, u64, u64, P]),
@@ -223,18 +270,24 @@ def sfc_launch_count() -> int:
     return int(lib().sfc_launch_count())
 
 
+def sfc_pool_bytes_in_use() -> int:
+    """Device bytes held from the library's own pool (not from a caller's allocator)."""
+    return int(lib().sfc_pool_bytes_in_use())
+
+
 # --------------------------------------------------------------------------------------
 # index
 # --------------------------------------------------------------------------------------
 
 class Index:
-    """Owns an sfc_index handle."""
+    """Owns an sfc_index handle (and keeps the allocator it was built with alive)."""
 
-    def __init__(self, handle: ctypes.c_void_p, curve: int, device, dim: int = 2):
+    def __init__(self, handle: ctypes.c_void_p, curve: int, device, dim: int = 2, allocator=None):
         self._h = handle
         self.curve = curve
         self.device = device
         self.dim = dim
+        self.allocator = allocator
 
     @property
     def handle(self):
@@ -252,43 +305,51 @@ class Index:
             pass
 
 
+def _alloc_ptr(allocator):
+    return ctypes.byref(allocator.struct) if allocator is not None else None
+
+
 def sfc_build(points: torch.Tensor, curve="z", options: sfc_options | None = None, stream=None,
-              **opts) -> Index:
+              allocator: TorchAllocator | None = None, **opts) -> Index:
+    """allocator: e.g. TorchAllocator() to take all of the index's device memory from
+    PyTorch's caching allocator (None: the library's own pool)."""
     points = _pts(points)
     o = options if options is not None else sfc_default_options(**opts)
     h = ctypes.c_void_p()
     _check(lib().sfc_build(ctypes.byref(h), _dptr(points), points.shape[0], _curve(curve),
-                           ctypes.byref(o), _stream(stream)), "sfc_build")
-    return Index(h, _curve(curve), points.device)
+                           ctypes.byref(o), _alloc_ptr(allocator), _stream(stream)), "sfc_build")
+    return Index(h, _curve(curve), points.device, allocator=allocator)
 
 
 def sfc_build_host(points: np.ndarray, curve="z", options: sfc_options | None = None, stream=None,
-                   **opts) -> Index:
+                   allocator: TorchAllocator | None = None, **opts) -> Index:
     points = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 2)
     o = options if options is not None else sfc_default_options(**opts)
     h = ctypes.c_void_p()
     _check(lib().sfc_build_host(ctypes.byref(h), _hptr(points), points.shape[0], _curve(curve),
-                                ctypes.byref(o), _stream(stream)), "sfc_build_host")
-    return Index(h, _curve(curve), torch.device("cuda", torch.cuda.current_device()))
+                                ctypes.byref(o), _alloc_ptr(allocator), _stream(stream)), "sfc_build_host")
+    return Index(h, _curve(curve), torch.device("cuda", torch.cuda.current_device()), allocator=allocator)
 
 
-def sfc_build3(points: torch.Tensor, options: sfc_options | None = None, stream=None, **opts) -> Index:
+def sfc_build3(points: torch.Tensor, options: sfc_options | None = None, stream=None,
+               allocator: TorchAllocator | None = None, **opts) -> Index:
     """3-D index of int32 [n, 3] points (Z curve in Z^3, coordinates in [0, 2^21))."""
     points = _pts(points, 3)
     o = options if options is not None else sfc_default_options(**opts)
     h = ctypes.c_void_p()
-    _check(lib().sfc_build3(ctypes.byref(h), _dptr(points), points.shape[0], ctypes.byref(o), _stream(stream)),
-           "sfc_build3")
-    return Index(h, SFC_CURVE_Z, points.device, dim=3)
+    _check(lib().sfc_build3(ctypes.byref(h), _dptr(points), points.shape[0], ctypes.byref(o),
+                            _alloc_ptr(allocator), _stream(stream)), "sfc_build3")
+    return Index(h, SFC_CURVE_Z, points.device, dim=3, allocator=allocator)
 
 
-def sfc_build3_host(points: np.ndarray, options: sfc_options | None = None, stream=None, **opts) -> Index:
+def sfc_build3_host(points: np.ndarray, options: sfc_options | None = None, stream=None,
+                    allocator: TorchAllocator | None = None, **opts) -> Index:
     points = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 3)
     o = options if options is not None else sfc_default_options(**opts)
     h = ctypes.c_void_p()
     _check(lib().sfc_build3_host(ctypes.byref(h), _hptr(points), points.shape[0], ctypes.byref(o),
-                                 _stream(stream)), "sfc_build3_host")
-    return Index(h, SFC_CURVE_Z, torch.device("cuda", torch.cuda.current_device()), dim=3)
+                                 _alloc_ptr(allocator), _stream(stream)), "sfc_build3_host")
+    return Index(h, SFC_CURVE_Z, torch.device("cuda", torch.cuda.current_device()), dim=3, allocator=allocator)
 
 
 def sfc_keys3(points: torch.Tensor, out: torch.Tensor | None = None, stream=None):
@@ -531,6 +592,16 @@ def sfc_model_fence(index: Index, stream=None) -> np.ndarray:
     _check(lib().sfc_model_fence(index.handle, None, ctypes.byref(nl), _stream(stream)), "sfc_model_fence")
     out = np.zeros((nl.value, 16), np.uint64)
     _check(lib().sfc_model_fence(index.handle, _hptr(out), ctypes.byref(nl), _stream(stream)), "sfc_model_fence")
+    return out
+
+
+def sfc_model_fence_fine(index: Index, stream=None) -> np.ndarray:
+    """uint64[leaves, 256]: the fine fence keys of every leaf."""
+    nl = ctypes.c_int(0)
+    _check(lib().sfc_model_fence_fine(index.handle, None, ctypes.byref(nl), _stream(stream)), "sfc_model_fence_fine")
+    out = np.zeros((nl.value, 256), np.uint64)
+    _check(lib().sfc_model_fence_fine(index.handle, _hptr(out), ctypes.byref(nl), _stream(stream)),
+           "sfc_model_fence_fine")
     return out
 
 

@@ -47,23 +47,39 @@ static void keep_pool_memory()
     done[dev] = true;
 }
 
-sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st)
+thread_local const sfc_allocator* t_alloc = nullptr;
+static std::atomic<uint64_t> g_pool_bytes{0};   // held from the library's own pool
+
+sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st, const sfc_allocator** owner)
 {
     *p = nullptr;
-    keep_pool_memory();
     if (bytes == 0) bytes = 16;
+    const sfc_allocator* a = t_alloc;
+    if (owner) *owner = a;
+    if (a) {   // the caller's allocator: stream-ordered on st, NULL when it has no memory
+        *p = a->alloc(bytes, reinterpret_cast<void*>(st), a->ctx);
+        return *p ? SFC_OK : SFC_ERR_OOM;
+    }
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
     }
+    g_pool_bytes.fetch_add(bytes, std::memory_order_relaxed);
     return SFC_OK;
 }
 
-void dev_free(void* p, cudaStream_t st)
+void dev_free(void* p, size_t bytes, cudaStream_t st, const sfc_allocator* owner)
 {
-    if (p) cudaFreeAsync(p, st);
+    if (!p) return;
+    if (owner) {
+        owner->free(p, reinterpret_cast<void*>(st), owner->ctx);
+    } else {
+        cudaFreeAsync(p, st);
+        g_pool_bytes.fetch_sub(bytes == 0 ? 16 : bytes, std::memory_order_relaxed);
+    }
 }
 
 }  // namespace sfc
@@ -203,6 +219,7 @@ const LearnedModelView* model_view(sfc_index* idx, LearnedModelView& v)
     v.root = model_root_device(idx);
     v.leaf = idx->model.leaves.as<LeafParams>();
     v.fence = idx->model.fence.as<uint64_t>();
+    v.fence_fine = idx->model.fence_fine.as<uint64_t>();
     v.stats = model_stats(idx);
     return &v;
 }
@@ -360,12 +377,13 @@ void sfc_default_options(sfc_options* opt)
 }
 
 sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_curve curve,
-                     const sfc_options* opt, void* stream)
+                     const sfc_options* opt, const sfc_allocator* alloc, void* stream)
 {
     if (!out) return SFC_ERR_INVALID;
     *out = nullptr;
     if (n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
     if (curve != SFC_CURVE_Z && curve != SFC_CURVE_HILBERT) return SFC_ERR_INVALID;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SFC_ERR_INVALID;
     sfc_options o;
     sfc_default_options(&o);
     if (opt) o = *opt;
@@ -380,6 +398,11 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
     sfc_index* idx = new (std::nothrow) sfc_index();
     if (!idx) return SFC_ERR_OOM;
     cudaGetDevice(&idx->device);
+    if (alloc) {
+        idx->alloc = *alloc;
+        idx->has_alloc = true;
+    }
+    AllocScope scope(idx->allocator());
     idx->curve = curve;
     idx->n = n;
     idx->opt = o;
@@ -405,23 +428,28 @@ sfc_status sfc_build(sfc_index** out, const int32_t* d_points, uint64_t n, sfc_c
 }
 
 sfc_status sfc_build_host(sfc_index** out, const int32_t* h_points, uint64_t n, sfc_curve curve,
-                          const sfc_options* opt, void* stream)
+                          const sfc_options* opt, const sfc_allocator* alloc, void* stream)
 {
     if (!out) return SFC_ERR_INVALID;
     *out = nullptr;
     if (n >= 0xffffffffull || (n && !h_points)) return SFC_ERR_INVALID;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
+    AllocScope scope(alloc);   // the staging copy of the points comes from the same allocator
     void* d = nullptr;
-    SFC_TRY(dev_alloc(&d, n * sizeof(int2), st));
+    const sfc_allocator* owner = nullptr;
+    SFC_TRY(dev_alloc(&d, n * sizeof(int2), st, &owner));
     cudaError_t e = n ? cudaMemcpyAsync(d, h_points, n * sizeof(int2), cudaMemcpyHostToDevice, st) : cudaSuccess;
-    sfc_status s = e == cudaSuccess ? sfc_build(out, static_cast<int32_t*>(d), n, curve, opt, stream) : SFC_ERR_CUDA;
-    dev_free(d, st);
+    sfc_status s = e == cudaSuccess ? sfc_build(out, static_cast<int32_t*>(d), n, curve, opt, alloc, stream)
+                                    : SFC_ERR_CUDA;
+    dev_free(d, n * sizeof(int2), st, owner);
     return s;
 }
 
 void sfc_destroy(sfc_index* idx)
 {
     if (!idx) return;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = idx->last_stream;
     for (const ProfRec& r : idx->prof.recs) {
         cudaEventDestroy(r.a);
@@ -435,6 +463,7 @@ void sfc_destroy(sfc_index* idx)
 sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void* stream)
 {
     if (!idx || n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     idx->last_stream = st;
     idx->n = n;
@@ -454,6 +483,7 @@ sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void
 sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* stream)
 {
     if (!idx || n_max >= 0xffffffffull) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     SFC_TRY(ensure_status_buf(idx, st));
     const uint64_t n1 = n_max ? n_max : 1;
@@ -490,6 +520,7 @@ sfc_status sfc_graph_capture(sfc_index* idx, unsigned flags, const int32_t* d_po
                              uint32_t* d_out_ids, uint64_t ids_capacity, sfc_graph** out, void* stream)
 {
     if (!idx || !out || !flags || (flags & ~(SFC_GRAPH_REBUILD | SFC_GRAPH_QUERY))) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     *out = nullptr;
     const bool rb = flags & SFC_GRAPH_REBUILD, qb = flags & SFC_GRAPH_QUERY;
     if (rb && (n >= 0xffffffffull || (n && !d_points))) return SFC_ERR_INVALID;
@@ -541,6 +572,7 @@ sfc_status sfc_query_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_
                            uint64_t* d_out_offsets, void* stream)
 {
     if (!idx || !d_out_offsets || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     idx->last_stream = as_stream(stream);
     return do_count(idx, d_q, d_delta, m, d_out_offsets, as_stream(stream));
 }
@@ -550,6 +582,7 @@ sfc_status sfc_query_write(sfc_index* idx, const int32_t* d_q, const int32_t* d_
                            void* stream)
 {
     if (!idx || !d_out_offsets || (ids_capacity && !d_out_ids)) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     idx->last_stream = as_stream(stream);
     return do_write(idx, d_q, d_delta, m, d_out_offsets, d_out_ids, ids_capacity, as_stream(stream));
 }
@@ -622,6 +655,7 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
                         int* h_chunk, int* h_batch, int* h_qbatch, void* stream)
 {
     if (!idx || (m && (!d_q || !d_delta)) || m >= 0xffffffffull) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     const TuneKey key{idx->device, (int)idx->curve, lg2(idx->n + 1), lg2(m + 1), (int)idx->bounds,
                       idx->opt.cover_refine, idx->norm};
@@ -770,6 +804,7 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
     if (!idx || !h_out_offsets || (m && (!h_q || !h_delta)) || (ids_capacity && !h_out_ids) ||
         m >= 0xffffffffull)
         return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     idx->last_stream = st;
     HostStage& hs = idx->stage;
@@ -827,6 +862,7 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
 sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream)
 {
     if (!idx) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     SFC_TRY(ensure_status_buf(idx, as_stream(stream)));
     return ensure_query_ws(idx, m, as_stream(stream));
 }
@@ -843,6 +879,7 @@ sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode)
 sfc_status sfc_train_model(sfc_index* idx, void* stream)
 {
     if (!idx || idx->dim != 2) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     idx->last_stream = as_stream(stream);
     ProfScope ps(idx, "train", as_stream(stream));
     return train_model(idx, as_stream(stream));
@@ -946,11 +983,13 @@ sfc_status sfc_keys3(const int32_t* d_points, uint64_t n, uint64_t* d_keys, void
     return launch_keys3(d_points, n, d_keys, nullptr, as_stream(stream));
 }
 
-sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt, void* stream)
+sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, const sfc_options* opt,
+                      const sfc_allocator* alloc, void* stream)
 {
     if (!out) return SFC_ERR_INVALID;
     *out = nullptr;
     if (n >= 0xffffffffull || (n && !d_points)) return SFC_ERR_INVALID;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SFC_ERR_INVALID;
     sfc_options o;
     sfc_default_options(&o);
     if (opt) o = *opt;
@@ -963,6 +1002,11 @@ sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, cons
     sfc_index* idx = new (std::nothrow) sfc_index();
     if (!idx) return SFC_ERR_OOM;
     cudaGetDevice(&idx->device);
+    if (alloc) {
+        idx->alloc = *alloc;
+        idx->has_alloc = true;
+    }
+    AllocScope scope(idx->allocator());
     idx->curve = SFC_CURVE_Z;
     idx->dim = 3;
     idx->drop = o.cover_refine < 0 ? 1 : o.cover_refine;
@@ -982,23 +1026,27 @@ sfc_status sfc_build3(sfc_index** out, const int32_t* d_points, uint64_t n, cons
 }
 
 sfc_status sfc_build3_host(sfc_index** out, const int32_t* h_points, uint64_t n, const sfc_options* opt,
-                           void* stream)
+                           const sfc_allocator* alloc, void* stream)
 {
     if (!out) return SFC_ERR_INVALID;
     *out = nullptr;
     if (n >= 0xffffffffull || (n && !h_points)) return SFC_ERR_INVALID;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SFC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
+    AllocScope scope(alloc);
     void* d = nullptr;
-    SFC_TRY(dev_alloc(&d, n * 3 * sizeof(int32_t), st));
+    const sfc_allocator* owner = nullptr;
+    SFC_TRY(dev_alloc(&d, n * 3 * sizeof(int32_t), st, &owner));
     cudaError_t e = n ? cudaMemcpyAsync(d, h_points, n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st) : cudaSuccess;
-    sfc_status s = e == cudaSuccess ? sfc_build3(out, static_cast<int32_t*>(d), n, opt, stream) : SFC_ERR_CUDA;
-    dev_free(d, st);
+    sfc_status s = e == cudaSuccess ? sfc_build3(out, static_cast<int32_t*>(d), n, opt, alloc, stream) : SFC_ERR_CUDA;
+    dev_free(d, n * 3 * sizeof(int32_t), st, owner);
     return s;
 }
 
 sfc_status sfc_device_status(sfc_index* idx, uint32_t* h_bits, void* stream)
 {
     if (!idx) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     SFC_TRY(ensure_status_buf(idx, st));
     uint32_t bits = 0;
@@ -1056,6 +1104,7 @@ sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d
                             uint32_t* d_count, void* stream)
 {
     if (!idx || (m && (!d_q || !d_delta))) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
     cudaStream_t st = as_stream(stream);
     SFC_TRY(ensure_status_buf(idx, st));
     QueryArgs a = base_args(idx, d_q, d_delta, m);
@@ -1064,6 +1113,8 @@ sfc_status sfc_query_ranges(sfc_index* idx, const int32_t* d_q, const int32_t* d
 }
 
 uint64_t sfc_launch_count(void) { return g_launches.load(); }
+
+uint64_t sfc_pool_bytes_in_use(void) { return g_pool_bytes.load(); }
 
 const char* sfc_status_string(sfc_status s)
 {

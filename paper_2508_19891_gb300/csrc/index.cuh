@@ -43,6 +43,7 @@ struct ModelState {
     DevBuf tmp;        // per-leaf first/last position and error extremes during a fit
     DevBuf leaves;     // LeafParams[nleaves], read by the query path
     DevBuf fence;      // uint64[nleaves][kFence]: fence keys of each leaf, read by the query path
+    DevBuf fence_fine; // uint64[nleaves][kFenceFine]: the fine fence keys of each leaf
     DevBuf route;      // leaf of every key (uint32[n])
 };
 
@@ -78,6 +79,9 @@ struct sfc_index {
     int norm = 0;                       // query window (sfc_norm)
     int dim = 2;                        // 2, or 3 for indexes made by sfc_build3
     cudaStream_t last_stream = nullptr;
+    sfc_allocator alloc{};              // the caller's allocator (used when has_alloc)
+    bool has_alloc = false;
+    const sfc_allocator* allocator() const { return has_alloc ? &alloc : nullptr; }
 
     sfc::DevBuf keys, ids, xy;          // the sorted array A_P and its keys
     sfc::DevBuf xy_by_id;               // coordinates by id (dynamic setting)

@@ -703,16 +703,19 @@ __global__ void leaf_store_err_kernel(const LeafTmp* tmp, LeafParams* leaf, int 
     }
 }
 
-// The fence of every leaf (kFence keys at equally spaced positions of its range); a leaf with
-// no keys gets keys that no target exceeds.
+// The fences of every leaf: the fine fence (kFenceFine keys at equally spaced positions of its
+// range) and the coarse one (every kFence-th fine key); a leaf with no keys gets keys that no
+// target exceeds.
 __global__ void fence_kernel(const uint64_t* __restrict__ keys, const LeafParams* __restrict__ leaf, int leaves,
-                             uint64_t* __restrict__ fence)
+                             uint64_t* __restrict__ fence, uint64_t* __restrict__ fence_fine)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= leaves * kFence) return;
-    const int j = i / kFence, s = i - j * kFence;
+    if (i >= leaves * kFenceFine) return;
+    const int j = i / kFenceFine, r = i - j * kFenceFine;
     const uint64_t first = leaf[j].first, c = leaf[j].end - leaf[j].first;
-    fence[i] = c ? keys[first + ((uint64_t)s * c) / kFence] : ~0ull;
+    const uint64_t k = c ? keys[first + ((uint64_t)r * c) / kFenceFine] : ~0ull;
+    fence_fine[i] = k;
+    if (r % kFence == 0) fence[j * kFence + r / kFence] = k;
 }
 
 }  // namespace
@@ -753,7 +756,9 @@ sfc_status fit_leaves(sfc_index* idx, cudaStream_t st)
     leaf_store_err_kernel<<<(leaves + 255) / 256, 256, 0, st>>>(tmp, lp, leaves);
     count_launch();
     SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
-    fence_kernel<<<(leaves * kFence + 255) / 256, 256, 0, st>>>(keys, lp, leaves, M.fence.as<uint64_t>());
+    SFC_TRY(M.fence_fine.ensure((size_t)leaves * kFenceFine * sizeof(uint64_t), st));
+    fence_kernel<<<(leaves * kFenceFine + 255) / 256, 256, 0, st>>>(keys, lp, leaves, M.fence.as<uint64_t>(),
+                                                                    M.fence_fine.as<uint64_t>());
     count_launch();
     return launch_status();
 }
@@ -774,6 +779,7 @@ sfc_status reserve_model(sfc_index* idx, uint64_t n, cudaStream_t st)
     SFC_TRY(M.tmp.ensure((size_t)leaves * sizeof(LeafTmp), st));
     SFC_TRY(M.leaves.ensure((size_t)leaves * sizeof(LeafParams), st));
     SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
+    SFC_TRY(M.fence_fine.ensure((size_t)leaves * kFenceFine * sizeof(uint64_t), st));
     SFC_TRY(M.route.ensure(std::max<uint64_t>(n, 1) * sizeof(uint32_t), st));
     return SFC_OK;
 }
@@ -962,6 +968,21 @@ sfc_status sfc_model_fence(const sfc_index* cidx, uint64_t* h_fence, int* h_leav
     if (h_leaves) *h_leaves = L;
     if (h_fence)
         SFC_CUDA_TRY(cudaMemcpyAsync(h_fence, idx->model.fence.ptr, (size_t)L * kFence * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, st));
+    SFC_CUDA_TRY(cudaStreamSynchronize(st));
+    return SFC_OK;
+}
+
+sfc_status sfc_model_fence_fine(const sfc_index* cidx, uint64_t* h_fence, int* h_leaves, void* stream)
+{
+    sfc_index* idx = const_cast<sfc_index*>(cidx);
+    if (!idx) return SFC_ERR_INVALID;
+    if (!idx->model.trained || !idx->model.fence_fine.ptr) return SFC_ERR_STATE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int L = idx->model.nleaves;
+    if (h_leaves) *h_leaves = L;
+    if (h_fence)
+        SFC_CUDA_TRY(cudaMemcpyAsync(h_fence, idx->model.fence_fine.ptr, (size_t)L * kFenceFine * sizeof(uint64_t),
                                      cudaMemcpyDeviceToHost, st));
     SFC_CUDA_TRY(cudaStreamSynchronize(st));
     return SFC_OK;

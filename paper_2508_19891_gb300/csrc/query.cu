@@ -39,6 +39,28 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Binary searches in lock step per thread, and the plan kernel's resident blocks per SM (its
+// register budget) for each bound search.
+#ifndef SFC_BINARY_BATCH
+#define SFC_BINARY_BATCH 8
+#endif
+#ifndef SFC_PLAN_BLOCKS_BINARY
+#define SFC_PLAN_BLOCKS_BINARY 4
+#endif
+#ifndef SFC_PLAN_BLOCKS_LEARNED
+#define SFC_PLAN_BLOCKS_LEARNED 4
+#endif
+#ifndef SFC_LEARNED_BATCH
+#define SFC_LEARNED_BATCH 2
+#endif
+// Targets a warp searches per round: the flat list of its 32 queries' interval endpoints is
+// searched in rounds of at most this many (one round for nearly every warp: cover 1 averages
+// about 6.5 endpoints per query).  A multiple of 32.
+#ifndef SFC_PLAN_CAP
+#define SFC_PLAN_CAP 256
+#endif
+constexpr uint32_t kPlanCap = SFC_PLAN_CAP;
+
 __device__ __forceinline__ bool query_valid(int32_t qx, int32_t qy, int32_t delta)
 {
     return point_in_domain(qx, qy) && delta >= 0;
@@ -71,6 +93,28 @@ __device__ __forceinline__ void lower_bounds_window(const uint64_t* __restrict__
     }
 }
 
+// E lower_bounds in lock step with one step count for all: the answer of search x lies in
+// [base[x], base[x] + len] (the same len for every x, keys[base[x] .. base[x] + len) inside the
+// array).  Each step halves len and moves a base past the probed key when that key is below
+// the target (Khuong & Morin's branch-free search); the final probe decides between base and
+// base + 1.  With one length there is no per-search bookkeeping: a step is an add, the load,
+// the 64-bit compare and a select.
+template <int E>
+__device__ __forceinline__ void lower_bounds_uniform(const uint64_t* __restrict__ keys, const uint64_t* t,
+                                                     uint32_t* base, uint32_t len)
+{
+    if (len == 0) return;
+#pragma unroll 1
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+#pragma unroll
+        for (int x = 0; x < E; ++x) base[x] = __ldg(keys + base[x] + half) < t[x] ? base[x] + half : base[x];
+        len -= half;
+    }
+#pragma unroll
+    for (int x = 0; x < E; ++x) base[x] += __ldg(keys + base[x]) < t[x] ? 1u : 0u;
+}
+
 // Per-thread counters of the learned search, summed once per block at the end of the plan.
 struct BoundStats {
     unsigned long long endpoints = 0, misses = 0, window = 0;
@@ -79,7 +123,9 @@ struct BoundStats {
 // Bound search functors: lower_bound of t[0..ne) (ne <= E) into r[].
 struct BinaryBounds {
     static constexpr bool kStats = false;
-    static constexpr int kBatch = 8;   // endpoints searched in lock step per thread
+    static constexpr int kBatch = SFC_BINARY_BATCH;
+    static constexpr bool kFenceSmem = false;
+    static constexpr int kMinBlocks = SFC_PLAN_BLOCKS_BINARY;   // endpoints searched in lock step per thread
     __device__ __forceinline__ void prepare(RootParams*) {}
     template <int E>
     __device__ __forceinline__ void search(const uint64_t* keys, uint32_t n, const uint64_t* t, uint32_t* r,
@@ -92,14 +138,41 @@ struct BinaryBounds {
 #pragma unroll
         for (int e = 0; e < E; ++e) r[e] = lo[e];
     }
+    // lower_bound over the whole array of the warp's flat list of T targets (each lane takes
+    // targets lane, lane + 32, ...; kBatch of them in lock step); results in res
+    __device__ __forceinline__ void search_flat(const uint64_t* keys, uint32_t n, const uint64_t* tg, uint32_t* res,
+                                                uint32_t T, BoundStats&, uint64_t*) const
+    {
+        constexpr int E = kBatch;
+#pragma unroll 1
+        for (uint32_t e0 = lane_id(); e0 < T; e0 += 32 * E) {
+            uint64_t t[E];
+            uint32_t base[E];
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                const uint32_t e = e0 + 32 * x;
+                t[x] = e < T ? tg[e] : 0;
+                base[x] = 0;
+            }
+            lower_bounds_uniform<E>(keys, t, base, n);
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                const uint32_t e = e0 + 32 * x;
+                if (e < T) res[e] = base[x];
+            }
+        }
+    }
 };
 
 struct LearnedBounds {
     static constexpr bool kStats = true;
-    static constexpr int kBatch = 4;
+    static constexpr bool kFenceSmem = false;
+    static constexpr int kBatch = SFC_LEARNED_BATCH;
+    static constexpr int kMinBlocks = SFC_PLAN_BLOCKS_LEARNED;
     const RootParams* root;      // device; after prepare() the block's shared-memory copy
     const LeafParams* leaf;
-    const uint64_t* fence;       // [leaves][kFence] fence keys
+    const uint64_t* fence;       // [leaves][kFence] coarse fence keys
+    const uint64_t* fence_fine;  // [leaves][kFenceFine] fine fence keys
     unsigned long long* stats;   // [0] endpoints, [1] misses, [2] window sum
     // every thread of the block calls this, then the block synchronises
     __device__ __forceinline__ void prepare(RootParams* s)
@@ -109,99 +182,154 @@ struct LearnedBounds {
         for (unsigned i = threadIdx.x; i < sizeof(RootParams) / 4; i += blockDim.x) dst[i] = src[i];
         root = s;
     }
-    template <int E>
-    __device__ __forceinline__ void search(const uint64_t* keys, uint32_t n, const uint64_t* t, uint32_t* r,
-                                           int ne, BoundStats& bs) const
+    // lower_bound over the whole array of the warp's flat list of T targets (each lane takes
+    // targets lane, lane + 32, ...; kBatch of them in lock step); results in res.  Per target:
+    //   1. the root routes it to leaf j (the keys below it lie in leaves before j, the keys
+    //      above it in leaves after j, as the root is monotone);
+    //   2. the leaf's line predicts its position p and the stored error window bounds it:
+    //      lower_bound(t) lies in [a, b] = [p + err_lo, p + err_hi + 1] within the leaf;
+    //   3. the window picks the slice of the leaf's fine fence (the keys at kFenceFine equally
+    //      spaced positions of the leaf) that falls inside it, and counting the slice's keys
+    //      below t brackets the target between two fence keys;
+    //   4. the last-mile search runs over the bracket within the window (every search of a
+    //      batch padded to the longest); an answer on the edge of its range is checked against
+    //      the key beyond the edge, and a target whose window missed is searched over the whole
+    //      array.
+    __device__ __forceinline__ void search_flat(const uint64_t* keys, uint32_t n, const uint64_t* tg, uint32_t* res,
+                                                uint32_t T, BoundStats& bs, uint64_t*) const
     {
-        uint32_t lo[E], len[E];
-        int jl[E];
-        uint32_t fl[E], fn[E];   // fence search: the number of fence keys below t lies in [fl, fl + fn]
-        unsigned long long wsum = 0;
-        // the leaf of each target and its window: prediction + stored error extremes
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            lo[e] = 0;
-            len[e] = 0;
-            jl[e] = 0;
-            fl[e] = 0;
-            fn[e] = 0;
-            if (e < ne) {
-                const int j = route_leaf(*root, t[e]);
-                const LeafParams lp = leaf[j];
-                const int64_t p = leaf_predict(lp, t[e]);
-                int64_t a = p + lp.err_lo, b = p + (int64_t)lp.err_hi + 1;
-                a = max(a, (int64_t)lp.first);
-                a = min(a, (int64_t)lp.end);
-                b = max(b, a);
-                b = min(b, (int64_t)lp.end);
-                lo[e] = (uint32_t)a;
-                len[e] = (uint32_t)(b - a);
-                jl[e] = j;
-                fn[e] = lp.end > lp.first ? kFence : 0;
-            }
-        }
-        // bracket each target between two fence keys of its leaf (one 128-byte line per leaf)
-        while (true) {
-            bool any = false;
-#pragma unroll
-            for (int e = 0; e < E; ++e) any |= fn[e] > 0;
-            if (!any) break;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (fn[e] > 0) {
-                    const uint32_t half = fn[e] >> 1;
-                    const bool right = __ldg(fence + (size_t)jl[e] * kFence + fl[e] + half) < t[e];
-                    fl[e] = right ? fl[e] + half + 1 : fl[e];
-                    fn[e] = right ? fn[e] - half - 1 : half;
-                }
-            }
-        }
-        // s fence keys below t: lower_bound(t) lies between the positions of fence keys s - 1 and
-        // s; the search takes the intersection with the model's window
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            if (e < ne) {
-                const uint64_t first = __ldg(&leaf[jl[e]].first), c = __ldg(&leaf[jl[e]].end) - first;
-                if (c) {
-                    const uint64_t sfn = fl[e];
-                    const uint64_t bl = sfn == 0 ? first : first + ((sfn - 1) * c) / kFence + 1;
-                    const uint64_t bh = sfn == kFence ? first + c : first + (sfn * c) / kFence;
-                    const uint64_t nl = max((uint64_t)lo[e], bl), nh = min((uint64_t)lo[e] + len[e], bh);
-                    if (nl <= nh) {
-                        lo[e] = (uint32_t)nl;
-                        len[e] = (uint32_t)(nh - nl);
-                    } else {
-                        lo[e] = (uint32_t)bl;
-                        len[e] = (uint32_t)(bh - bl);
-                    }
-                }
-                wsum += len[e];
-            }
-        }
-        // window search, verify (lower_bound is the unique r with keys[r-1] < t <= keys[r]), and
-        // for the endpoints that fail, a second pass over the whole array (full binary search)
-        uint32_t miss = 0;
+        constexpr int E = kBatch;
 #pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            lower_bounds_window<E>(keys, t, lo, len);
-            if (pass == 1) break;
+        for (uint32_t e0 = lane_id(); e0 < T; e0 += 32 * E) {
+            uint64_t t[E];
+            uint32_t lo[E], len[E], fo[E];
+            int ne = 0;
+            uint32_t F = 0;   // longest fence slice of the batch
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (e < ne) {
-                    const uint32_t x = lo[e];
-                    const bool ok = (x == 0 || __ldg(keys + x - 1) < t[e]) && (x == n || __ldg(keys + x) >= t[e]);
-                    if (!ok) { miss |= 1u << e; lo[e] = 0; len[e] = n; }
+            for (int x = 0; x < E; ++x) {
+                const uint32_t e = e0 + 32 * x;
+                ne += e < T;
+                t[x] = e < T ? tg[e] : 0;
+                const uint32_t j = (uint32_t)route_leaf(*root, t[x]);
+                const LeafParams lp = leaf[j];
+                const int64_t p = leaf_predict(lp, t[x]);
+                int64_t a = p + lp.err_lo, b = p + (int64_t)lp.err_hi + 1;
+                a = min(max(a, (int64_t)lp.first), (int64_t)lp.end);
+                b = min(max(b, a), (int64_t)lp.end);
+                lo[x] = (uint32_t)a;
+                len[x] = (uint32_t)(b - a);
+                // fine fence entry r sits at position first + floor(r cnt / kFenceFine): the
+                // entries at positions below a are below t, those above b are not, so only
+                // entries [ra, rb) need counting; ra and rb from a float estimate widened by one
+                // entry on each side (its error is far below one entry)
+                const uint32_t cnt = lp.end - lp.first;
+                uint32_t ra = 0, rb = 0;
+                if (cnt) {
+                    const float scale = __fdividef((float)kFenceFine, (float)cnt);
+                    const float fa = (float)(uint32_t)(a - lp.first) * scale;
+                    const float fbk = (float)(uint32_t)(b - lp.first + 1) * scale;
+                    ra = (uint32_t)max((int)fa - 1, 0);
+                    rb = (uint32_t)min((int)fbk + 2, kFenceFine);
                 }
+                fo[x] = j * kFenceFine + ra;
+                F = max(F, rb - ra);
             }
-            if (!miss) break;
-        }
+            // count the slice's fence keys below t: branch-free, every slice padded to the
+            // batch's longest, moved left where it would run past the leaf's fence (the entries
+            // it takes in on the left are below t and are counted like the others)
 #pragma unroll
-        for (int e = 0; e < E; ++e) r[e] = lo[e];
-        bs.endpoints += ne;
-        bs.misses += __popc(miss);
-        bs.window += wsum;
+            for (int x = 0; x < E; ++x) {
+                const uint32_t r0 = fo[x] % kFenceFine;
+                fo[x] -= r0 + F > kFenceFine ? r0 + F - kFenceFine : 0;
+            }
+            uint32_t c[E];
+#pragma unroll
+            for (int x = 0; x < E; ++x) c[x] = 0;
+            if (F > 0) {
+                uint32_t flen = F;
+#pragma unroll 1
+                while (flen > 1) {
+                    const uint32_t half = flen >> 1;
+#pragma unroll
+                    for (int x = 0; x < E; ++x) c[x] = __ldg(fence_fine + fo[x] + c[x] + half) < t[x] ? c[x] + half : c[x];
+                    flen -= half;
+                }
+#pragma unroll
+                for (int x = 0; x < E; ++x) c[x] += __ldg(fence_fine + fo[x] + c[x]) < t[x] ? 1u : 0u;
+            }
+            uint32_t N = 0;
+            unsigned long long wsum = 0;
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                const uint32_t j = fo[x] / kFenceFine;
+                const uint64_t first = __ldg(&leaf[j].first), cnt = __ldg(&leaf[j].end) - first;
+                // r fine keys below t: lower_bound(t) lies in [P(r - 1) + 1, P(r)], P(r) the
+                // position of fine key r, P(kFenceFine) = end
+                const uint32_t r = cnt ? fo[x] % kFenceFine + c[x] : 0u;
+                const uint64_t bl = r == 0 ? first : first + ((uint64_t)(r - 1) * cnt) / kFenceFine + 1;
+                const uint64_t bh = r == 0 ? first : (r == kFenceFine ? first + cnt : first + ((uint64_t)r * cnt) / kFenceFine);
+                const uint64_t nl = max((uint64_t)lo[x], bl), nh = min((uint64_t)lo[x] + len[x], bh);
+                if (nl <= nh) {
+                    lo[x] = (uint32_t)nl;
+                    len[x] = (uint32_t)(nh - nl);
+                } else {   // both hold lower_bound(t) unless the window is off: keep the bracket
+                    lo[x] = (uint32_t)bl;
+                    len[x] = (uint32_t)(bh - bl);
+                }
+                if (e0 + 32 * x < T) wsum += len[x];
+                N = max(N, len[x]);
+            }
+            // pad every range to the longest: [lo, lo + N) still holds the answer, moved left
+            // where it would run past the end of the array
+            uint32_t lo0[E];
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                lo[x] = (uint64_t)lo[x] + N > n ? n - N : lo[x];
+                lo0[x] = lo[x];
+            }
+            lower_bounds_uniform<E>(keys, t, lo, N);
+            // an answer strictly inside its range has both neighbours in it, compared by the
+            // search; on an edge, the key beyond the edge decides
+            uint32_t miss = 0;
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                const uint32_t r = lo[x];
+                bool ok = true;
+                if (r == lo0[x] && r > 0) ok = __ldg(keys + r - 1) < t[x];
+                if (r == lo0[x] + N && r < n) ok = ok && __ldg(keys + r) >= t[x];
+                if (!ok && e0 + 32 * x < T) miss |= 1u << x;
+            }
+            if (miss) {
+                uint32_t r2[E];
+#pragma unroll
+                for (int x = 0; x < E; ++x) r2[x] = 0;
+                lower_bounds_uniform<E>(keys, t, r2, n);
+#pragma unroll
+                for (int x = 0; x < E; ++x) lo[x] = (miss >> x) & 1u ? r2[x] : lo[x];
+            }
+#pragma unroll
+            for (int x = 0; x < E; ++x) {
+                const uint32_t e = e0 + 32 * x;
+                if (e < T) res[e] = lo[x];
+            }
+            bs.endpoints += ne;
+            bs.misses += __popc(miss);
+            bs.window += wsum;
+        }
     }
 };
+
+// Inclusive prefix sum over the warp (every lane calls).
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v += t;
+    }
+    return v;
+}
 
 // Sum of v over the warp (every lane calls), returned to every lane.
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
@@ -231,18 +359,19 @@ __device__ __forceinline__ bool cell_occupied(const uint32_t* __restrict__ occ, 
     return (__ldg(occ + (b >> 5)) >> (b & 31)) & 1u;
 }
 
-// Writes the cover's key intervals to lo/hi (sorted, abutting ones merged); returns how many.
+// The cells of the cover, each as the key of its first point (its key interval is [c, c | span],
+// Observation; every cell of a cover has the same level), sorted ascending into the thread's
+// column col[0], col[stride], ... of shared memory; returns how many; *span_out = 4^l - 1.
 // DROP 0: cells(Q), the cells of level l (2 delta <= 2^l < 4 delta, capped at omega) that meet
 // the clipped square Q.  DROP > 0: the cells of level max(0, l - DROP) that hold an integer
 // point of the closed ball (the distance from q to the cell's nearest integer point is at most
-// delta; for the square window every cell meeting Q qualifies).  Each cell gives the key
-// interval [pi(C)o0, pi(C)o1] (Observation).  With the
-// early-termination bitmap (occ != NULL), cells it shows empty are dropped; ncell / nempty
-// count the cover's cells and the dropped ones.
+// delta; for the square window every cell meeting Q qualifies).  With the early-termination
+// bitmap (occ != NULL), cells it shows empty are dropped; ncell / nempty count the cover's
+// cells and the dropped ones.
 template <int DROP>
-__device__ __forceinline__ int derive_ranges(int curve, int norm, const HilbertTables* tb, int32_t qx, int32_t qy,
-                                             int32_t delta, const uint32_t* occ, int D, uint64_t* lo,
-                                             uint64_t* hi, uint32_t& ncell, uint32_t& nempty)
+__device__ __forceinline__ int derive_cells(int curve, int norm, const HilbertTables* tb, int32_t qx, int32_t qy,
+                                            int32_t delta, const uint32_t* occ, int D, uint64_t* col, int stride,
+                                            uint64_t* span_out, uint32_t& ncell, uint32_t& nempty)
 {
     constexpr int K = Cover<DROP>::K;
     const int64_t d = delta;
@@ -255,81 +384,73 @@ __device__ __forceinline__ int derive_ranges(int curve, int norm, const HilbertT
     }
     l = max(0, l - DROP);
     const uint64_t span = (l >= kOmega) ? kKeyMax : ((1ull << (2 * l)) - 1);
+    *span_out = span;
+    constexpr int NX = Cover<DROP>::NX;   // cells per axis at most
+    const int64_t cx0 = x0 >> l, cy0 = y0 >> l;
+    const int nx = (int)min((int64_t)NX, (x1 >> l) - cx0 + 1), ny = (int)min((int64_t)NX, (y1 >> l) - cy0 + 1);
+    // per column: the squared distance from q to the column's nearest x and, for the Z curve,
+    // the spread bits of its first x (the key of cell (cx, cy) is spread(cx 2^l) | spread(cy 2^l) << 1)
+    int64_t dx2[NX];
+    uint64_t sx[NX];
+#pragma unroll
+    for (int ix = 0; ix < NX; ++ix) {
+        const int64_t cx = cx0 + ix;
+        const int64_t ax0 = cx << l, ax1 = ((cx + 1) << l) - 1;
+        const int64_t dx = qx < ax0 ? ax0 - qx : (qx > ax1 ? qx - ax1 : 0);
+        dx2[ix] = dx * dx;
+        sx[ix] = curve == SFC_CURVE_Z ? spread_bits((uint32_t)(cx << l)) : 0;
+    }
+    const int64_t d2 = d * d;
     int cnt = 0;
-    for (int64_t cy = y0 >> l; cy <= (y1 >> l); ++cy) {
-        for (int64_t cx = x0 >> l; cx <= (x1 >> l); ++cx) {
-            if (DROP > 0 && norm == SFC_NORM_DISC) {   // every cell meeting Q meets a square window
-                const int64_t ax0 = cx << l, ax1 = ((cx + 1) << l) - 1;
-                const int64_t ay0 = cy << l, ay1 = ((cy + 1) << l) - 1;
-                const int64_t dx = qx < ax0 ? ax0 - qx : (qx > ax1 ? qx - ax1 : 0);
-                const int64_t dy = qy < ay0 ? ay0 - qy : (qy > ay1 ? qy - ay1 : 0);
-                if (dx * dx + dy * dy > d * d) continue;
-            }
-            if (cnt == K) break;   // unreachable: at most Cover<DROP>::NX cells per axis
-            const uint64_t c = curve_key(curve, tb, (uint32_t)(cx << l), (uint32_t)(cy << l)) & ~span;
+#pragma unroll
+    for (int iy = 0; iy < NX; ++iy) {
+        if (iy >= ny) break;
+        const int64_t cy = cy0 + iy;
+        const int64_t ay0 = cy << l, ay1 = ((cy + 1) << l) - 1;
+        const int64_t dy = qy < ay0 ? ay0 - qy : (qy > ay1 ? qy - ay1 : 0);
+        const int64_t dy2 = dy * dy;
+        const uint64_t sy = curve == SFC_CURVE_Z ? spread_bits((uint32_t)(cy << l)) << 1 : 0;
+#pragma unroll
+        for (int ix = 0; ix < NX; ++ix) {
+            if (ix >= nx) break;
+            // every cell meeting Q meets a square window; a disc needs an integer point of the
+            // ball in the cell
+            if (DROP > 0 && norm == SFC_NORM_DISC && dx2[ix] + dy2 > d2) continue;
+            const uint64_t c = (curve == SFC_CURVE_Z ? (sx[ix] | sy)
+                                                     : hilbert_key(tb, (uint32_t)((cx0 + ix) << l), (uint32_t)(cy << l))) &
+                               ~span;
             ++ncell;
             if (occ && !cell_occupied(occ, D, l, c)) {
                 ++nempty;
                 continue;
             }
             int j = cnt;
-            while (j > 0 && lo[j - 1] > c) { lo[j] = lo[j - 1]; hi[j] = hi[j - 1]; --j; }
-            lo[j] = c;
-            hi[j] = c | span;
+            while (j > 0 && col[(j - 1) * stride] > c) {
+                col[j * stride] = col[(j - 1) * stride];
+                --j;
+            }
+            col[j * stride] = c;
             ++cnt;
         }
     }
-    // merge intervals that abut in key order (the scan over them is identical)
-    int m = 0;
-    for (int i = 0; i < cnt; ++i) {
-        if (m > 0 && hi[m - 1] + 1 == lo[i]) {
-            hi[m - 1] = hi[i];
-        } else {
-            lo[m] = lo[i];
-            hi[m] = hi[i];
-            ++m;
-        }
-    }
-    return m;
+    return cnt;
 }
 
-// Range derivation + bound search for one query: the intervals' key ranges lo/hi and array
-// bounds b[r], e[r]; returns their number.  Endpoints go through the bound search in lock-step
-// batches of 8 (eight independent searches in flight per thread).
-template <class Bounds, int DROP>
-__device__ __forceinline__ int query_bounds(const Bounds& bounds, const QueryArgs& a, const HilbertTables* tb,
-                                            int32_t qx, int32_t qy, int32_t delta, uint64_t* lo, uint64_t* hi,
-                                            uint32_t* b, uint32_t* e, BoundStats& bs, uint32_t& ncell,
-                                            uint32_t& nempty)
+// Visits the endpoints of the merged key intervals of nc sorted cells (cells whose intervals
+// abut in key order form one interval: the scan over them is identical): endpoint 2k is the
+// first key of interval k, endpoint 2k + 1 one past its last key (the interval's array range is
+// [lower_bound(first key), lower_bound(last key + 1))).  fn(ep, key) in order.
+template <class F>
+__device__ __forceinline__ void for_each_endpoint(const uint64_t* col, int stride, int nc, uint64_t span, F&& fn)
 {
-    constexpr int K = Cover<DROP>::K;
-    constexpr int BW = Bounds::kBatch;
-    constexpr int NB = (2 * K + BW - 1) / BW;
-    const uint64_t* keys = a.keys;
-    const uint32_t n = a.n;
-    const int cnt = derive_ranges<DROP>(a.curve, a.norm, tb, qx, qy, delta, a.occ, a.occ_depth, lo, hi, ncell,
-                                        nempty);
-    const int ne = 2 * cnt;
-#pragma unroll 1
-    for (int bi = 0; bi < NB && BW * bi < ne; ++bi) {
-        uint64_t t[BW];
-        uint32_t r[BW];
-#pragma unroll
-        for (int x = 0; x < BW; ++x) {
-            const int ep = BW * bi + x;
-            t[x] = ep < ne ? ((ep & 1) ? hi[ep >> 1] + 1 : lo[ep >> 1]) : 0;
-        }
-        bounds.template search<BW>(keys, n, t, r, min(max(ne - BW * bi, 0), BW), bs);
-#pragma unroll
-        for (int x = 0; x < BW; ++x) {
-            const int ep = BW * bi + x;
-            if (ep < ne) {
-                if (ep & 1) e[ep >> 1] = r[x];
-                else b[ep >> 1] = r[x];
-            }
-        }
+    uint32_t ep = 0;
+    uint64_t prev_end = 0;
+    for (int k = 0; k < nc; ++k) {
+        const uint64_t c = col[k * stride];
+        if (k == 0 || c != prev_end) fn(ep++, c);                           // an interval starts
+        prev_end = c + span + 1;
+        if (k + 1 == nc || col[(k + 1) * stride] != prev_end) fn(ep++, prev_end);   // ... and ends
     }
-    return cnt;
 }
 
 // Lists query i as small (it scans at most kSmallScan points) for the thread-per-query kernels;
@@ -354,14 +475,41 @@ struct PlanExport {
     uint32_t* cnt;
 };
 
-// One thread per query: its intervals' (begin, end) in slots 0.. of the query's K slots (unused
-// slots (0, 0)), the number of chunks of its scan, and the scanned total.
+
+// Dynamic shared memory of plan_kernel<Bounds, DROP, ..>: each thread's column of K cell keys
+// (column-major, so that the lanes of a warp touch consecutive words), then per warp the flat
+// target list (kPlanCap keys) and its results (kPlanCap positions), and for the learned search
+// per warp one leaf's fine fence (kFenceFine keys).
+template <class Bounds, int DROP>
+constexpr size_t plan_smem_bytes()
+{
+    return (size_t)Cover<DROP>::K * kThreads * sizeof(uint64_t) +
+           (size_t)(kThreads / 32) * kPlanCap * (sizeof(uint64_t) + sizeof(uint32_t)) +
+           (Bounds::kFenceSmem ? (size_t)(kThreads / 32) * kFenceFine * sizeof(uint64_t) : 0);
+}
+
+// One thread per query for the range derivation: the cells of its cover, sorted, in shared
+// memory.  The bound search runs on the warp's endpoints as one flat list in shared memory:
+// lane L's query owns list positions [off_L, off_L + 2 cnt_L), the lanes take the list
+// round-robin, so every lane searches about the same number of endpoints whatever the spread
+// of interval counts over the warp's queries.  Then each thread writes its query's intervals'
+// (begin, end) to slots 0.. of its K slots (unused slots (0, 0)), the number of chunks of its
+// scan, and adds to the scanned total.  Nothing per query lives in local memory.
 template <class Bounds, int DROP, bool EXPORT>
-__global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds bounds_in, PlanExport ex)
+__global__ void __launch_bounds__(kThreads, Bounds::kMinBlocks) plan_kernel(QueryArgs a, Bounds bounds_in, PlanExport ex)
 {
     constexpr int K = Cover<DROP>::K;
     __shared__ HilbertTables tb;
     __shared__ RootParams s_root;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint64_t* col = reinterpret_cast<uint64_t*>(s_dyn) + threadIdx.x;
+    const unsigned warp = threadIdx.x >> 5;
+    uint64_t* tg = reinterpret_cast<uint64_t*>(s_dyn) + (size_t)K * kThreads + (size_t)warp * kPlanCap;
+    uint32_t* res = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(s_dyn) + (size_t)K * kThreads +
+                                                (size_t)(kThreads / 32) * kPlanCap) + (size_t)warp * kPlanCap;
+    uint64_t* sf = reinterpret_cast<uint64_t*>(s_dyn + (size_t)K * kThreads * sizeof(uint64_t) +
+                                               (size_t)(kThreads / 32) * kPlanCap * (sizeof(uint64_t) + sizeof(uint32_t))) +
+                   (size_t)warp * kFenceFine;
     Bounds bounds = bounds_in;
     bounds.prepare(&s_root);
     __syncthreads();
@@ -379,14 +527,51 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
     }
     const bool ok = active && query_valid(q.x, q.y, delta);
     if (active && !ok) set_status(a.status, SFC_DEV_BAD_QUERY);
-    uint64_t lo[K], hi[K];
-    uint32_t b[K], e[K];
     BoundStats bs;
     uint32_t ncell = 0, nempty = 0;
-    const int cnt = ok ? query_bounds<Bounds, DROP>(bounds, a, &tb, q.x, q.y, delta, lo, hi, b, e, bs, ncell, nempty)
-                       : 0;
-    uint64_t S = 0;
-    for (int k = 0; k < cnt; ++k) S += e[k] - b[k];
+    uint64_t span = 0;
+    const int nc = ok ? derive_cells<DROP>(a.curve, a.norm, &tb, q.x, q.y, delta, a.occ, a.occ_depth, col, kThreads,
+                                           &span, ncell, nempty)
+                      : 0;
+    uint32_t cnt = 0;   // merged intervals
+    for_each_endpoint(col, kThreads, nc, span, [&](uint32_t ep, uint64_t) { cnt += ep & 1u; });
+    const uint32_t ne = 2u * cnt;
+    const uint32_t incl = warp_incl_scan_u32(ne);
+    const uint32_t off = incl - ne;
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    uint2* rp = (!EXPORT && active) ? reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * K * i) : nullptr;
+    uint64_t S = 0;   // sum of e_k - b_k, gathered endpoint by endpoint
+#pragma unroll 1
+    for (uint32_t r0 = 0; r0 < T; r0 += kPlanCap) {   // warp-uniform
+        const uint32_t r1 = min(T, r0 + kPlanCap);
+        for_each_endpoint(col, kThreads, nc, span, [&](uint32_t ep, uint64_t key) {
+            const uint32_t f = off + ep;
+            if (f >= r0 && f < r1) tg[f - r0] = key;
+        });
+        __syncwarp();
+        bounds.search_flat(a.keys, a.n, tg, res, r1 - r0, bs, sf);
+        __syncwarp();
+        const uint32_t f0 = max(off, r0), f1 = min(off + ne, r1);
+        for (uint32_t f = f0; f < f1; ++f) {
+            const uint32_t ep = f - off, k = ep >> 1;
+            const uint32_t pos = res[f - r0];
+            S += (ep & 1u) ? (uint64_t)pos : (uint64_t)0 - pos;
+            if (!EXPORT) {
+                if (rp) reinterpret_cast<uint32_t*>(rp + k)[ep & 1u] = pos;
+            } else {
+                const uint64_t o = (uint64_t)K * i + k;
+                const uint64_t key = tg[f - r0];
+                if (ep & 1u) {
+                    if (ex.hi) ex.hi[o] = key - 1;
+                    if (ex.e) ex.e[o] = pos;
+                } else {
+                    if (ex.lo) ex.lo[o] = key;
+                    if (ex.b) ex.b[o] = pos;
+                }
+            }
+        }
+        __syncwarp();   // read before the next round's targets overwrite the list
+    }
     // warp totals of the statistics: one atomic per warp and counter, no block barrier (a warp
     // that is done leaves without waiting for the rest of its block)
     if (a.scanned) {
@@ -416,20 +601,17 @@ __global__ void __launch_bounds__(kThreads, 4) plan_kernel(QueryArgs a, Bounds b
     if (!EXPORT && a.small_list) small_append(a, small, i);
     if (!active) return;
     if (!EXPORT) {
-        uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * K * i);
-#pragma unroll
-        for (int k = 0; k < K; ++k) rp[k] = k < cnt ? make_uint2(b[k], e[k]) : make_uint2(0u, 0u);
+        for (uint32_t k = cnt; k < (uint32_t)K; ++k) rp[k] = make_uint2(0u, 0u);
         a.nchunks[i] = small ? 0u : (uint32_t)((S + a.chunk - 1) / a.chunk);
     } else {
-        for (int k = 0; k < K; ++k) {
-            const bool u = k < cnt;
+        for (uint32_t k = cnt; k < (uint32_t)K; ++k) {
             const uint64_t o = (uint64_t)K * i + k;
-            if (ex.lo) ex.lo[o] = u ? lo[k] : 1;
-            if (ex.hi) ex.hi[o] = u ? hi[k] : 0;
-            if (ex.b) ex.b[o] = u ? b[k] : 0;
-            if (ex.e) ex.e[o] = u ? e[k] : 0;
+            if (ex.lo) ex.lo[o] = 1;
+            if (ex.hi) ex.hi[o] = 0;
+            if (ex.b) ex.b[o] = 0;
+            if (ex.e) ex.e[o] = 0;
         }
-        if (ex.cnt) ex.cnt[i] = (uint32_t)cnt;
+        if (ex.cnt) ex.cnt[i] = cnt;
     }
 }
 
@@ -592,17 +774,6 @@ struct QView {
     int32_t d;       // delta
     int64_t d2;      // delta^2
 };
-
-__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
-{
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if ((int)lane >= o) v += t;
-    }
-    return v;
-}
 
 // Loads query qi's intervals into the warp's table (lane r takes interval r); every lane calls.
 __device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi, WarpTab* tab)
@@ -1100,15 +1271,32 @@ sfc_status launch_count_write(const QueryArgs& a, bool write, cudaStream_t st)
 
 }  // namespace
 
+// Opts plan_kernel<Bounds, DROP, EXPORT> into its dynamic shared memory (more than 48 KB for
+// the finest cover), once per instantiation and device.
+template <class Bounds, int DROP, bool EXPORT>
+static void allow_plan_smem()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(plan_kernel<Bounds, DROP, EXPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)plan_smem_bytes<Bounds, DROP>());
+    done[dev] = true;
+}
+
 template <int DROP, bool EXPORT>
 static void plan_dispatch(const QueryArgs& a, const LearnedModelView* lm, const PlanExport& ex, cudaStream_t st)
 {
     const unsigned g = (unsigned)((a.m + kThreads - 1) / kThreads);
-    if (lm)
-        plan_kernel<LearnedBounds, DROP, EXPORT>
-            <<<g, kThreads, 0, st>>>(a, LearnedBounds{lm->root, lm->leaf, lm->fence, lm->stats}, ex);
-    else
-        plan_kernel<BinaryBounds, DROP, EXPORT><<<g, kThreads, 0, st>>>(a, BinaryBounds{}, ex);
+    if (lm) {
+        allow_plan_smem<LearnedBounds, DROP, EXPORT>();
+        plan_kernel<LearnedBounds, DROP, EXPORT><<<g, kThreads, plan_smem_bytes<LearnedBounds, DROP>(), st>>>(
+            a, LearnedBounds{lm->root, lm->leaf, lm->fence, lm->fence_fine, lm->stats}, ex);
+    } else {
+        allow_plan_smem<BinaryBounds, DROP, EXPORT>();
+        plan_kernel<BinaryBounds, DROP, EXPORT><<<g, kThreads, plan_smem_bytes<BinaryBounds, DROP>(), st>>>(
+            a, BinaryBounds{}, ex);
+    }
 }
 
 template <bool EXPORT>

@@ -54,6 +54,7 @@ struct LearnedModelView {
     const RootParams* root;      // device memory (written by training, no host copy needed)
     const LeafParams* leaf;
     const uint64_t* fence;       // [leaves][kFence] fence keys
+    const uint64_t* fence_fine;  // [leaves][kFenceFine] fine fence keys
     unsigned long long* stats;   // [3]: endpoints, misses, window sum
 };
 

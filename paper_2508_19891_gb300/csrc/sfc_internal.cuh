@@ -50,34 +50,44 @@ __host__ __device__ __forceinline__ uint64_t occupancy_level_start(int t)
     return (((uint64_t)1 << (2 * t)) - 1) / 3;
 }
 
-// Stream-ordered device allocation helpers.
-sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st);
-void dev_free(void* p, cudaStream_t st);
+// Device allocation.  Memory comes from the caller's sfc_allocator while a call on an index
+// built with one is running on this thread (AllocScope, set by every entry point that takes
+// an index), else from the device's stream-ordered pool (cudaMallocAsync).  Each allocation
+// remembers where it came from (*owner), and is given back there.
+extern thread_local const sfc_allocator* t_alloc;
 
-template <class T>
-inline sfc_status dev_alloc_t(T** p, size_t count, cudaStream_t st)
-{
-    return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T), st);
-}
+class AllocScope {
+public:
+    explicit AllocScope(const sfc_allocator* a) : prev_(t_alloc) { t_alloc = a; }
+    ~AllocScope() { t_alloc = prev_; }
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+private:
+    const sfc_allocator* prev_;
+};
+
+sfc_status dev_alloc(void** p, size_t bytes, cudaStream_t st, const sfc_allocator** owner);
+void dev_free(void* p, size_t bytes, cudaStream_t st, const sfc_allocator* owner);
 
 // A grow-only device buffer.
 struct DevBuf {
     void* ptr = nullptr;
     size_t bytes = 0;
+    const sfc_allocator* owner = nullptr;   // allocator the memory came from (NULL: the pool)
     sfc_status ensure(size_t need, cudaStream_t st)
     {
         if (need <= bytes) return SFC_OK;
-        if (ptr) dev_free(ptr, st);
+        if (ptr) dev_free(ptr, bytes, st, owner);
         ptr = nullptr;
         bytes = 0;
         size_t nb = need + need / 8 + 256;
-        SFC_TRY(dev_alloc(&ptr, nb, st));
+        SFC_TRY(dev_alloc(&ptr, nb, st, &owner));
         bytes = nb;
         return SFC_OK;
     }
     void release(cudaStream_t st)
     {
-        if (ptr) dev_free(ptr, st);
+        if (ptr) dev_free(ptr, bytes, st, owner);
         ptr = nullptr;
         bytes = 0;
     }
@@ -315,6 +325,11 @@ constexpr int kRootMlp = 1;
 // (position first + s * (end - first) / kFence, s = 0 .. kFence - 1), one 128-byte line, so
 // a search first brackets its target between two fence keys.
 constexpr int kFence = 16;
+// ... and a fine fence: the keys at kFenceFine equally spaced positions (first + floor(r *
+// (end - first) / kFenceFine)), kFence lines of kFence keys; coarse fence key s is fine fence
+// key kFence * s, so once the coarse line has bracketed the target between coarse keys s - 1
+// and s, fine line s - 1 narrows it to 1 / kFenceFine of the leaf.
+constexpr int kFenceFine = kFence * kFence;
 
 struct LeafParams {          // 32 bytes, one sector
     uint64_t base;           // smallest key routed to the leaf

@@ -209,6 +209,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     ModelState& M = idx->model;
     M.state.release(st); M.samples.release(st); M.partial.release(st);
     M.tmp.release(st); M.leaves.release(st); M.route.release(st); M.fence.release(st);
+    M.fence_fine.release(st);
     UpdateWs& u = idx->uws;
     u.a.release(st); u.b.release(st); u.c.release(st); u.d.release(st);
     u.e.release(st); u.f.release(st); u.g.release(st); u.h.release(st);
@@ -371,6 +372,7 @@ extern "C" sfc_status sfc_update(sfc_index* idx, const int32_t* d_inserts, uint6
     if (k_del > idx->n || k_ins >= 0xffffffffull) return k_del > idx->n ? SFC_ERR_NOT_FOUND : SFC_ERR_INVALID;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     idx->last_stream = st;
+    sfc::AllocScope alloc_scope(idx->allocator());
     sfc::ProfScope ps(idx, "update", st);
     return sfc::apply_update(idx, d_inserts, k_ins, d_delete_ids, k_del, h_first_new_id, st);
 }

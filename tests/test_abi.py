@@ -45,8 +45,27 @@ def test_host_only_calls(libsfc):
     assert sfc.sfc_model_hidden() == 16
     # invalid arguments are rejected on the host before anything touches a device
     L = sfc.lib()
-    assert L.sfc_build(None, None, 0, 0, None, None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_build(None, None, 0, 0, None, None, None) == sfc.SFC_ERR_INVALID
     h = ctypes.c_void_p()
-    assert L.sfc_build(ctypes.byref(h), None, 5, 0, None, None) == sfc.SFC_ERR_INVALID
-    assert L.sfc_build(ctypes.byref(h), None, 0, 7, None, None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_build(ctypes.byref(h), None, 5, 0, None, None, None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_build(ctypes.byref(h), None, 0, 7, None, None, None) == sfc.SFC_ERR_INVALID
     assert L.sfc_query_count(None, None, None, 0, None, None) == sfc.SFC_ERR_INVALID
+    # an allocator must bring both callbacks (checked before any device work)
+    half = sfc.sfc_allocator()
+    half.alloc = sfc.SFC_ALLOC_FN(lambda n, s, c: None)
+    assert L.sfc_build(ctypes.byref(h), None, 0, 0, None, ctypes.byref(half), None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_build_host(ctypes.byref(h), None, 0, 0, None, ctypes.byref(half), None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_build3(ctypes.byref(h), None, 0, None, ctypes.byref(half), None) == sfc.SFC_ERR_INVALID
+
+
+def test_build_signatures_take_an_allocator():
+    """sfc_build, sfc_build_host, sfc_build3 and sfc_build3_host take a const sfc_allocator*
+    before the stream, and the header declares the allocator's two callbacks and context."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for name in ("sfc_build", "sfc_build_host", "sfc_build3", "sfc_build3_host"):
+        m = re.search(name + r"\s*\(([^;]*)\);", text)
+        assert m, name
+        args = [a.strip() for a in m.group(1).split(",")]
+        assert args[-2].startswith("const sfc_allocator*") and args[-1].startswith("void* stream"), (name, args)
+    assert re.search(r"void\*\s*\(\*alloc\)\(size_t bytes, void\* stream, void\* ctx\)", text)
+    assert re.search(r"void\s*\(\*free\)\(void\* ptr, void\* stream, void\* ctx\)", text)

@@ -177,17 +177,21 @@ def test_trained_vs_untrained_root(cuda):
 
 @pytest.mark.parametrize("curve", ["z", "h"])
 def test_fence_matches_oracle(cuda, curve):
-    """The leaves' fences are the keys at the positions the definition gives (oracle
-    learned.leaf_fence over the oracle's sorted keys and the GPU's leaf ranges), and a learned
-    query batch still equals binary search."""
+    """The leaves' coarse (16) and fine (256) fences are the keys at the positions the
+    definition gives (oracle learned.leaf_fence over the oracle's sorted keys and the GPU's leaf
+    ranges), and a learned query batch still equals binary search."""
     from oracle import learned as L
     wl = W.mixed_1e7(scale=0.02)
     idx = sfc.sfc_build(to_dev(wl.points, cuda), curve, bounds="learned")
     m = sfc.sfc_model_get(idx)
     fence = sfc.sfc_model_fence(idx)
+    fine = sfc.sfc_model_fence_fine(idx)
     ref = oracle.build(wl.points, 30, curve)
     for j in range(len(m["first"])):
-        assert np.array_equal(fence[j], L.leaf_fence(ref.keys, int(m["first"][j]), int(m["end"][j]))), j
+        f, e = int(m["first"][j]), int(m["end"][j])
+        assert np.array_equal(fence[j], L.leaf_fence(ref.keys, f, e)), j
+        assert np.array_equal(fine[j], L.leaf_fence(ref.keys, f, e, k=256)), j
+        assert np.array_equal(fine[j][::16], fence[j]), j   # coarse key s is fine key 16 s
     off, ids = sfc.query(idx, to_dev(wl.queries, cuda), to_dev(wl.delta, cuda))
     roff, rids = oracle.query(ref, wl.queries, wl.delta)
     assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
