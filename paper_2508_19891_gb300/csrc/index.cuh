@@ -40,11 +40,10 @@ struct ModelState {
     DevBuf state;      // optimiser state and derived root parameters (layout in learned.cu)
     DevBuf samples;    // training sample x[N], y[N]
     DevBuf partial;    // per-block partial gradients and the completion counter
-    DevBuf tmp;        // per-leaf first/last position and error extremes during a fit
+    DevBuf tmp;        // leaf boundaries (uint32[nleaves + 1]) during a fit
     DevBuf leaves;     // LeafParams[nleaves], read by the query path
     DevBuf fence;      // uint64[nleaves][kFence]: fence keys of each leaf, read by the query path
     DevBuf fence_fine; // uint64[nleaves][kFenceFine]: the fine fence keys of each leaf
-    DevBuf route;      // leaf of every key (uint32[n])
 };
 
 struct ProfRec {

@@ -12,13 +12,15 @@
 //                        applies the update.  Piecewise-linear root: the per-knot gradient is
 //                        accumulated in 64-bit fixed point, so the sums are exact and the run
 //                        is deterministic; MLP root: fixed-order float reductions.
-//   route_kernel         leaf of every key (the query-time routing function) and the first /
-//                        last position of each leaf
-//   leaf_fix_kernel      empty leaves take the position where their keys would start
-//   leaf_fit_kernel      one block per leaf: least-squares line of position against key
-//                        offset (two passes, fp64 accumulators)
-//   leaf_err_kernel      exact min / max of (position - prediction) over each leaf's keys,
-//                        with the same fp32 predict function the queries call
+//   leaf_bounds_kernel   the root is monotone, so every leaf is a contiguous run of positions:
+//                        one binary search per leaf boundary over the sorted keys (routing
+//                        the probed keys) instead of routing every key; bound_max_kernel
+//                        keeps the boundaries in order
+//   leaf_stage_kernel    one block per leaf: least-squares line of position against key
+//                        offset (two passes, fp32 with the mean taken first), the exact
+//                        min / max of (position - prediction) over the leaf's keys with the
+//                        same fp32 predict function the queries call, and the leaf's coarse
+//                        (16) and fine (256) fences
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -53,12 +55,6 @@ struct TrainState {
     RootParams root;
 };
 
-struct LeafTmp {
-    uint32_t first;       // min position routed to the leaf
-    uint32_t last;        // max position routed to the leaf
-    int32_t err_lo;
-    int32_t err_hi;
-};
 
 // Derived root parameters from theta (one block; every thread calls it).
 __device__ void derive_root(TrainState* ts, int leaves)
@@ -494,228 +490,163 @@ __global__ void adam_kernel(TrainState* ts, float lr, int t, int np)
     adam_update(ts, lr);
 }
 
-__global__ void leaf_init_kernel(LeafTmp* tmp, int leaves)
-{
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < leaves; j += gridDim.x * blockDim.x) {
-        tmp[j].first = 0xffffffffu;
-        tmp[j].last = 0;
-        tmp[j].err_lo = 0x7fffffff;
-        tmp[j].err_hi = (int32_t)0x80000000;
-    }
-}
-
-// Leaf of every key with the query-time routing function; a position starts or ends a
-// leaf's run where its neighbour's leaf differs (one atomic per run, not per key).
-__global__ void __launch_bounds__(256) route_kernel(const uint64_t* __restrict__ keys, uint64_t n,
-                                                    const TrainState* ts, uint32_t* __restrict__ route,
-                                                    LeafTmp* tmp)
+// Leaf boundaries.  The root is monotone, so the keys routed to leaf j are the positions
+// [bound[j], bound[j + 1]) with bound[j] the first position whose key routes to a leaf >= j
+// (bound[0] = 0, bound[leaves] = n): one binary search per boundary over the sorted keys
+// instead of routing every key.  A leaf that no key routes to gets bound[j] = bound[j + 1].
+__global__ void __launch_bounds__(256) leaf_bounds_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+                                                          const TrainState* ts, int leaves, uint32_t* __restrict__ bound)
 {
     __shared__ RootParams s_root;
     for (unsigned w = threadIdx.x; w < sizeof(RootParams) / 4; w += blockDim.x)
         reinterpret_cast<uint32_t*>(&s_root)[w] = reinterpret_cast<const uint32_t*>(&ts->root)[w];
     __syncthreads();
-    const unsigned lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // four groups of the grid stride per iteration, their loads issued together (the loop
-    // bound is uniform per warp so the shuffles below see the whole warp)
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
-        uint64_t k[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + u * stride + threadIdx.x;
-            k[u] = i < n ? __ldg(keys + i) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + u * stride + threadIdx.x;
-            const bool ok = i < n;
-            const int j = ok ? route_leaf(s_root, k[u]) : -1;
-            int prev = __shfl_up_sync(0xffffffffu, j, 1);
-            if (lane == 0 && ok && i > 0) prev = route_leaf(s_root, keys[i - 1]);
-            int next = __shfl_down_sync(0xffffffffu, j, 1);
-            if ((lane == 31 || i + 1 >= n) && ok) next = (i + 1 < n) ? route_leaf(s_root, keys[i + 1]) : -1;
-            if (ok) {
-                route[i] = (uint32_t)j;
-                if (i == 0 || prev != j) atomicMin(&tmp[j].first, (uint32_t)i);
-                if (i + 1 == n || next != j) atomicMax(&tmp[j].last, (uint32_t)i);
-            }
-        }
-    }
-}
-
-// One block of 1024 threads: leaf params from the run bounds.  An empty leaf (no key routed
-// to it) takes first = end = the start of the next non-empty leaf (n past the last one): a
-// suffix minimum over the leaves, each thread owning a contiguous segment.
-__global__ void __launch_bounds__(1024) leaf_fix_kernel(const LeafTmp* tmp, int leaves, uint64_t n,
-                                                        LeafParams* out, const uint64_t* keys)
-{
-    __shared__ uint32_t s_min[1024];
-    const int T = blockDim.x, t = threadIdx.x;
-    const int per = (leaves + T - 1) / T;
-    const int j0 = t * per, j1 = min(leaves, j0 + per);
-    uint32_t m = 0xffffffffu;
-    for (int j = j0; j < j1; ++j)
-        if (tmp[j].first <= tmp[j].last) m = min(m, tmp[j].first);
-    s_min[t] = m;
-    __syncthreads();
-    // inclusive suffix-min over the threads' segment minima
-    for (int o = 1; o < T; o <<= 1) {
-        const uint32_t v = (t + o < T) ? s_min[t + o] : 0xffffffffu;
-        __syncthreads();
-        s_min[t] = min(s_min[t], v);
-        __syncthreads();
-    }
-    uint32_t next_start = (t + 1 < T) ? s_min[t + 1] : 0xffffffffu;
-    if (next_start == 0xffffffffu) next_start = (uint32_t)n;
-    for (int j = j1 - 1; j >= j0; --j) {
-        LeafParams lp;
-        if (tmp[j].first > tmp[j].last) {
-            lp.first = next_start;
-            lp.end = next_start;
-            lp.base = next_start < n ? keys[next_start] : kKeyMax;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > leaves) return;
+    uint64_t lo = 0, len = n;   // first position with route >= j lies in [lo, lo + len]
+    if (j == 0) len = 0;
+    else if (j == leaves) lo = n, len = 0;
+    while (len > 0) {
+        const uint64_t half = len >> 1;
+        if (route_leaf(s_root, __ldg(keys + lo + half)) < j) {
+            lo += half + 1;
+            len -= half + 1;
         } else {
-            lp.first = tmp[j].first;
-            lp.end = tmp[j].last + 1;
-            lp.base = keys[tmp[j].first];
-            next_start = min(next_start, tmp[j].first);
+            len = half;
         }
-        lp.slope = 0.0f;
-        lp.icpt = 0.0f;
-        lp.err_lo = 0;
-        lp.err_hi = 0;
-        out[j] = lp;
+    }
+    bound[j] = (uint32_t)lo;
+}
+
+// Running maximum of the boundaries (one block of 1024 threads, each owning a contiguous
+// segment), so that the leaves tile [0, n) in order even if fp32 rounding made the root
+// step down somewhere.
+__global__ void __launch_bounds__(1024) bound_max_kernel(uint32_t* bound, int count)
+{
+    __shared__ uint32_t s_max[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int per = (count + T - 1) / T;
+    const int j0 = t * per, j1 = min(count, j0 + per);
+    uint32_t m = 0;
+    for (int j = j0; j < j1; ++j) m = max(m, bound[j]);
+    s_max[t] = m;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {   // inclusive prefix max over the segments
+        const uint32_t v = t >= o ? s_max[t - o] : 0u;
+        __syncthreads();
+        s_max[t] = max(s_max[t], v);
+        __syncthreads();
+    }
+    uint32_t run = t > 0 ? s_max[t - 1] : 0u;
+    for (int j = j0; j < j1; ++j) {
+        run = max(run, bound[j]);
+        bound[j] = run;
     }
 }
 
-// One block per leaf: v = position - first against u = key - base over [first, end), in
-// fp32 with centred second pass and fixed-order tree reductions.  The line only places the
-// search window; the window itself is measured exactly afterwards (leaf_err_kernel).
-__global__ void __launch_bounds__(256) leaf_fit_kernel(const uint64_t* __restrict__ keys, LeafParams* leaf)
+// Block-wide int min / max (every thread calls it; result valid in all threads).
+__device__ int2 block_minmax_i(int lo, int hi, int* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[2 * warp] = lo;
+        sh[2 * warp + 1] = hi;
+    }
+    __syncthreads();
+    int a = 0x7fffffff, b = (int)0x80000000;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a = min(a, sh[2 * w]);
+        b = max(b, sh[2 * w + 1]);
+    }
+    return make_int2(a, b);
+}
+
+// One block per leaf j, over its positions [bound[j], bound[j + 1]):
+//   the least-squares line of position against key offset (v = position - first against
+//   u = key - base, base the leaf's smallest key; fp32 with the mean taken first and
+//   fixed-order reductions), then the exact error window: min and max of
+//   (position - prediction) over the leaf's keys with the query-time fp32 predict function,
+//   then its coarse and fine fences.  The leaf's keys are read three times; the later reads
+//   mostly come from L2.
+__global__ void __launch_bounds__(256) leaf_stage_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+                                                         const uint32_t* __restrict__ bound, LeafParams* leaf,
+                                                         uint64_t* __restrict__ fence,
+                                                         uint64_t* __restrict__ fence_fine)
 {
     __shared__ float sh[8];
-    LeafParams lp = leaf[blockIdx.x];
+    __shared__ int shi[16];
+    const int j = blockIdx.x;
+    LeafParams lp;
+    lp.first = bound[j];
+    lp.end = bound[j + 1];
+    lp.base = lp.first < n ? keys[lp.first] : kKeyMax;
+    lp.slope = 0.0f;
+    lp.icpt = 0.0f;
+    lp.err_lo = 0;
+    lp.err_hi = 0;
     const uint32_t cnt = lp.end - lp.first;
-    if (cnt < 2) {
-        if (threadIdx.x == 0) { leaf[blockIdx.x].slope = 0.0f; leaf[blockIdx.x].icpt = 0.0f; }
-        return;
-    }
-    // two passes (the mean first, for fp32 accuracy); each thread keeps four loads in flight
     const uint64_t* kp = keys + lp.first;
     const uint32_t B = blockDim.x;
-    float su = 0.0f;
-    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
-        float u[4];
+    if (cnt >= 2) {
+        // two passes (the mean first, for fp32 accuracy); each thread keeps four loads in flight
+        float su = 0.0f;
+        for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
+            float u[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t i = i0 + q * B;
-            u[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) : 0.0f;
-        }
-        su += (u[0] + u[1]) + (u[2] + u[3]);
-    }
-    const float mu = block_sum_f(su, sh) / (float)cnt;
-    const float mv = 0.5f * (float)(cnt - 1);   // mean of 0 .. cnt - 1
-    float sxy = 0.0f, sxx = 0.0f;
-    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
-        float du[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t i = i0 + q * B;
-            du[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) - mu : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t i = i0 + q * B;
-            if (i < cnt) {
-                sxy = fmaf(du[q], (float)i - mv, sxy);
-                sxx = fmaf(du[q], du[q], sxx);
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t i = i0 + q * B;
+                u[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) : 0.0f;
             }
+            su += (u[0] + u[1]) + (u[2] + u[3]);
         }
-    }
-    sxy = block_sum_f(sxy, sh);
-    sxx = block_sum_f(sxx, sh);
-    if (threadIdx.x == 0) {
-        const float slope = sxx > 0.0f ? sxy / sxx : 0.0f;
-        leaf[blockIdx.x].slope = slope;
-        leaf[blockIdx.x].icpt = mv - slope * mu;
-    }
-}
-
-__global__ void __launch_bounds__(256) leaf_err_kernel(const uint64_t* __restrict__ keys, uint64_t n,
-                                                       const uint32_t* __restrict__ route,
-                                                       const LeafParams* __restrict__ leaf, LeafTmp* tmp)
-{
-    const unsigned lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // four groups of the grid stride per iteration, their loads issued together
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += 4 * stride) {
-        uint64_t k[4];
-        uint32_t jr[4];
+        const float mu = block_sum_f(su, sh) / (float)cnt;
+        const float mv = 0.5f * (float)(cnt - 1);   // mean of 0 .. cnt - 1
+        float sxy = 0.0f, sxx = 0.0f;
+        for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
+            float du[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + u * stride + threadIdx.x;
-            k[u] = i < n ? __ldg(keys + i) : 0;
-            jr[u] = i < n ? __ldg(route + i) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + u * stride + threadIdx.x;
-            const bool ok = i < n;
-            int j = -1;
-            long long e = 0;
-            if (ok) {
-                j = (int)jr[u];
-                const LeafParams lp = leaf[j];
-                e = (long long)i - leaf_predict(lp, k[u]);
-                e = e > 0x7fffffffll ? 0x7fffffffll : (e < -0x7fffffffll ? -0x7fffffffll : e);
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t i = i0 + q * B;
+                du[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) - mu : 0.0f;
             }
-            // warp-aggregated when the whole warp is in one leaf (the common case)
-            const int j0 = __shfl_sync(0xffffffffu, j, 0);
-            const bool same = __all_sync(0xffffffffu, j == j0);
-            if (same) {
-                int lo = (int)e, hi = (int)e;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t i = i0 + q * B;
+                if (i < cnt) {
+                    sxy = fmaf(du[q], (float)i - mv, sxy);
+                    sxx = fmaf(du[q], du[q], sxx);
                 }
-                if (lane == 0 && j0 >= 0) {
-                    atomicMin(&tmp[j0].err_lo, lo);
-                    atomicMax(&tmp[j0].err_hi, hi);
-                }
-            } else if (ok) {
-                atomicMin(&tmp[j].err_lo, (int)e);
-                atomicMax(&tmp[j].err_hi, (int)e);
             }
         }
+        sxy = block_sum_f(sxy, sh);
+        sxx = block_sum_f(sxx, sh);
+        lp.slope = sxx > 0.0f ? sxy / sxx : 0.0f;
+        lp.icpt = mv - lp.slope * mu;
     }
-}
-
-__global__ void leaf_store_err_kernel(const LeafTmp* tmp, LeafParams* leaf, int leaves)
-{
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < leaves; j += gridDim.x * blockDim.x) {
-        if (tmp[j].err_lo <= tmp[j].err_hi) {
-            leaf[j].err_lo = tmp[j].err_lo;
-            leaf[j].err_hi = tmp[j].err_hi;
-        } else {   // no key routed here: the window is the (empty) leaf range itself
-            leaf[j].err_lo = 0;
-            leaf[j].err_hi = 0;
+    if (cnt >= 1) {
+        int lo = 0x7fffffff, hi = (int)0x80000000;
+        for (uint32_t i = threadIdx.x; i < cnt; i += B) {
+            long long e = (long long)(lp.first + i) - leaf_predict(lp, __ldg(kp + i));
+            e = e > 0x7fffffffll ? 0x7fffffffll : (e < -0x7fffffffll ? -0x7fffffffll : e);
+            lo = min(lo, (int)e);
+            hi = max(hi, (int)e);
         }
+        const int2 w = block_minmax_i(lo, hi, shi);
+        lp.err_lo = w.x;
+        lp.err_hi = w.y;
     }
-}
-
-// The fences of every leaf: the fine fence (kFenceFine keys at equally spaced positions of its
-// range) and the coarse one (every kFence-th fine key); a leaf with no keys gets keys that no
-// target exceeds.
-__global__ void fence_kernel(const uint64_t* __restrict__ keys, const LeafParams* __restrict__ leaf, int leaves,
-                             uint64_t* __restrict__ fence, uint64_t* __restrict__ fence_fine)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= leaves * kFenceFine) return;
-    const int j = i / kFenceFine, r = i - j * kFenceFine;
-    const uint64_t first = leaf[j].first, c = leaf[j].end - leaf[j].first;
-    const uint64_t k = c ? keys[first + ((uint64_t)r * c) / kFenceFine] : ~0ull;
-    fence_fine[i] = k;
-    if (r % kFence == 0) fence[j * kFence + r / kFence] = k;
+    for (uint32_t r = threadIdx.x; r < (uint32_t)kFenceFine; r += B) {
+        const uint64_t k = cnt ? __ldg(kp + ((uint64_t)r * cnt) / kFenceFine) : ~0ull;
+        fence_fine[(size_t)j * kFenceFine + r] = k;
+        if (r % kFence == 0) fence[(size_t)j * kFence + r / kFence] = k;
+    }
+    if (threadIdx.x == 0) leaf[j] = lp;
 }
 
 }  // namespace
@@ -732,33 +663,18 @@ sfc_status fit_leaves(sfc_index* idx, cudaStream_t st)
     const int leaves = M.nleaves;
     const uint64_t n = idx->n;
     TrainState* ts = M.state.as<TrainState>();
-    SFC_TRY(M.tmp.ensure((size_t)leaves * sizeof(LeafTmp), st));
+    SFC_TRY(M.tmp.ensure((size_t)(leaves + 1) * sizeof(uint32_t), st));
     SFC_TRY(M.leaves.ensure((size_t)leaves * sizeof(LeafParams), st));
-    SFC_TRY(M.route.ensure(std::max<uint64_t>(n, 1) * sizeof(uint32_t), st));
-    LeafTmp* tmp = M.tmp.as<LeafTmp>();
-    LeafParams* lp = M.leaves.as<LeafParams>();
-    const uint64_t* keys = idx->keys.as<uint64_t>();
-    const int g = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms() * 8));
-    leaf_init_kernel<<<(leaves + 255) / 256, 256, 0, st>>>(tmp, leaves);
-    count_launch();
-    if (n) {
-        route_kernel<<<g, 256, 0, st>>>(keys, n, ts, M.route.as<uint32_t>(), tmp);
-        count_launch();
-    }
-    leaf_fix_kernel<<<1, 1024, 0, st>>>(tmp, leaves, n, lp, keys);
-    count_launch();
-    leaf_fit_kernel<<<leaves, 256, 0, st>>>(keys, lp);
-    count_launch();
-    if (n) {
-        leaf_err_kernel<<<g, 256, 0, st>>>(keys, n, M.route.as<uint32_t>(), lp, tmp);
-        count_launch();
-    }
-    leaf_store_err_kernel<<<(leaves + 255) / 256, 256, 0, st>>>(tmp, lp, leaves);
-    count_launch();
     SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
     SFC_TRY(M.fence_fine.ensure((size_t)leaves * kFenceFine * sizeof(uint64_t), st));
-    fence_kernel<<<(leaves * kFenceFine + 255) / 256, 256, 0, st>>>(keys, lp, leaves, M.fence.as<uint64_t>(),
-                                                                    M.fence_fine.as<uint64_t>());
+    uint32_t* bound = M.tmp.as<uint32_t>();
+    const uint64_t* keys = idx->keys.as<uint64_t>();
+    leaf_bounds_kernel<<<(leaves + 1 + 255) / 256, 256, 0, st>>>(keys, n, ts, leaves, bound);
+    count_launch();
+    bound_max_kernel<<<1, 1024, 0, st>>>(bound, leaves + 1);
+    count_launch();
+    leaf_stage_kernel<<<leaves, 256, 0, st>>>(keys, n, bound, M.leaves.as<LeafParams>(), M.fence.as<uint64_t>(),
+                                              M.fence_fine.as<uint64_t>());
     count_launch();
     return launch_status();
 }
@@ -776,11 +692,10 @@ sfc_status reserve_model(sfc_index* idx, uint64_t n, cudaStream_t st)
     SFC_TRY(M.state.ensure(sizeof(TrainState), st));
     SFC_TRY(M.samples.ensure((size_t)N * 2 * sizeof(float), st));
     SFC_TRY(M.partial.ensure((size_t)kTrainBlocks * kPartial * sizeof(long long) + 256, st));
-    SFC_TRY(M.tmp.ensure((size_t)leaves * sizeof(LeafTmp), st));
+    SFC_TRY(M.tmp.ensure((size_t)(leaves + 1) * sizeof(uint32_t), st));
     SFC_TRY(M.leaves.ensure((size_t)leaves * sizeof(LeafParams), st));
     SFC_TRY(M.fence.ensure((size_t)leaves * kFence * sizeof(uint64_t), st));
     SFC_TRY(M.fence_fine.ensure((size_t)leaves * kFenceFine * sizeof(uint64_t), st));
-    SFC_TRY(M.route.ensure(std::max<uint64_t>(n, 1) * sizeof(uint32_t), st));
     return SFC_OK;
 }
 

@@ -8,7 +8,7 @@
 //                    plan: a digit that is the same for every key is skipped, and the
 //                    source/destination of each remaining pass is chosen on the device, so
 //                    the host never waits (the sort can be captured in a CUDA graph).
-//   3. onesweep_kernel, once per digit: each block takes the next tile (3072 keys), ranks
+//   3. onesweep_kernel, once per digit: each block takes the next tile (4096 keys), ranks
 //                    its keys per digit inside each warp with eight ballots (stable: item
 //                    order, then lane order), combines warps in shared memory, learns the
 //                    tile's global digit offsets by decoupled look-back over earlier tiles,
@@ -33,8 +33,15 @@ constexpr int kRadix = 1 << kBits;
 constexpr int kPasses = 8;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 12;
-constexpr int kTile = kThreads * kItems;        // 3072 keys per tile
+// keys per thread of a tile, and resident blocks per SM (the register budget) of a pass
+#ifndef SFC_SORT_ITEMS
+#define SFC_SORT_ITEMS 16
+#endif
+#ifndef SFC_SORT_BLOCKS
+#define SFC_SORT_BLOCKS 3
+#endif
+constexpr int kItems = SFC_SORT_ITEMS;
+constexpr int kTile = kThreads * kItems;        // 4096 keys per tile
 constexpr int kWarpSpan = 32 * kItems;          // 384 keys per warp
 
 struct PassPlan {
@@ -197,7 +204,7 @@ constexpr size_t kSortSmem = sizeof(uint64_t) * kTile + sizeof(uint32_t) * kTile
                              sizeof(HilbertTables);
 
 template <int CURVE>
-__global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(PassArgs a)
+__global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(PassArgs a)
 {
     const PassPlan pl = a.sm->plan[a.pass];
     if (!pl.active) return;

@@ -208,7 +208,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     }
     ModelState& M = idx->model;
     M.state.release(st); M.samples.release(st); M.partial.release(st);
-    M.tmp.release(st); M.leaves.release(st); M.route.release(st); M.fence.release(st);
+    M.tmp.release(st); M.leaves.release(st); M.fence.release(st);
     M.fence_fine.release(st);
     UpdateWs& u = idx->uws;
     u.a.release(st); u.b.release(st); u.c.release(st); u.d.release(st);
