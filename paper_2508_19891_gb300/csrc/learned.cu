@@ -574,13 +574,20 @@ __device__ int2 block_minmax_i(int lo, int hi, int* sh)
 //   (position - prediction) over the leaf's keys with the query-time fp32 predict function,
 //   then its coarse and fine fences.  The leaf's keys are read three times; the later reads
 //   mostly come from L2.
-__global__ void __launch_bounds__(256) leaf_stage_kernel(const uint64_t* __restrict__ keys, uint64_t n,
-                                                         const uint32_t* __restrict__ bound, LeafParams* leaf,
-                                                         uint64_t* __restrict__ fence,
-                                                         uint64_t* __restrict__ fence_fine)
+// Threads per leaf block: at 10^8 keys (about 24,000 per leaf) 512 threads take the stage from
+// 1.26 ms (256 threads) to 0.99 ms; 1,024 gain another 2%.
+#ifndef SFC_LEAF_THREADS
+#define SFC_LEAF_THREADS 512
+#endif
+constexpr int kLeafThreads = SFC_LEAF_THREADS;
+
+__global__ void __launch_bounds__(kLeafThreads) leaf_stage_kernel(const uint64_t* __restrict__ keys, uint64_t n,
+                                                                  const uint32_t* __restrict__ bound, LeafParams* leaf,
+                                                                  uint64_t* __restrict__ fence,
+                                                                  uint64_t* __restrict__ fence_fine)
 {
-    __shared__ float sh[8];
-    __shared__ int shi[16];
+    __shared__ float sh[kLeafThreads / 32];
+    __shared__ int shi[2 * (kLeafThreads / 32)];
     const int j = blockIdx.x;
     LeafParams lp;
     lp.first = bound[j];
@@ -673,8 +680,8 @@ sfc_status fit_leaves(sfc_index* idx, cudaStream_t st)
     count_launch();
     bound_max_kernel<<<1, 1024, 0, st>>>(bound, leaves + 1);
     count_launch();
-    leaf_stage_kernel<<<leaves, 256, 0, st>>>(keys, n, bound, M.leaves.as<LeafParams>(), M.fence.as<uint64_t>(),
-                                              M.fence_fine.as<uint64_t>());
+    leaf_stage_kernel<<<leaves, kLeafThreads, 0, st>>>(keys, n, bound, M.leaves.as<LeafParams>(),
+                                                       M.fence.as<uint64_t>(), M.fence_fine.as<uint64_t>());
     count_launch();
     return launch_status();
 }
