@@ -177,6 +177,13 @@ void sfc_destroy(sfc_index* idx);
  * after sfc_reserve it allocates nothing.  Errors as sfc_build. */
 sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void* stream);
 
+/* As sfc_rebuild with the points in host memory (int32[n][2], or [n][3] for a 3-D index):
+ * they are copied on the stream into a staging buffer that the index keeps (it only grows,
+ * and it comes from the index's allocator), then the index is rebuilt from it.  Page-locked
+ * h_points must stay unchanged until the stream has run the copy; pageable memory is copied
+ * before the call returns.  Errors as sfc_rebuild. */
+sfc_status sfc_rebuild_host(sfc_index* idx, const int32_t* h_points, uint64_t n, void* stream);
+
 /* Sizes every buffer of the index for rebuilds of up to n_max points and query batches of up
  * to m_max queries, so that later sfc_rebuild / sfc_query_* calls allocate nothing (needed
  * before capturing them in a CUDA graph). */

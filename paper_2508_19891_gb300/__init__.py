@@ -165,6 +165,7 @@ def lib():
             "sfc_pool_bytes_in_use": (u64, []),
             "sfc_autotune": (ci, [P, P, P, u64, ci, P, P, P, P]),
             "sfc_rebuild": (ci, [P, P, u64, P]),
+            "sfc_rebuild_host": (ci, [P, P, u64, P]),
             "sfc_reserve": (ci, [P, u64, u64, P]),
             "sfc_graph_capture": (ci, [P, ctypes.c_uint, P, u64, P, P, u64, P, P, u64, PP, P]),
             "sfc_graph_launch": (ci, [P, P]),
@@ -367,6 +368,14 @@ def sfc_destroy(index: Index):
 def sfc_rebuild(index: Index, points: torch.Tensor, stream=None):
     points = _pts(points, index.dim)
     _check(lib().sfc_rebuild(index.handle, _dptr(points), points.shape[0], _stream(stream)), "sfc_rebuild")
+
+
+def sfc_rebuild_host(index: Index, points: np.ndarray, stream=None):
+    """Rebuilds the index over host points (int32 [n, 2], or [n, 3] for a 3-D index); the
+    array must stay unchanged until the stream has run the copy when it is page-locked."""
+    points = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, index.dim)
+    _check(lib().sfc_rebuild_host(index.handle, _hptr(points), points.shape[0], _stream(stream)),
+           "sfc_rebuild_host")
 
 
 def sfc_reserve(index: Index, n_max: int, m_max: int, stream=None):

@@ -308,7 +308,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
 // The write pass for the queries [q_begin, q_end) of the pending count (no state checks).
 sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
                           const uint64_t* d_out_offsets, uint32_t* d_out_ids, uint64_t cap, cudaStream_t st,
-                          uint64_t q_begin, uint64_t q_end)
+                          uint64_t q_begin, uint64_t q_end, const uint32_t* perm = nullptr)
 {
     QueryWs& w = idx->qws;
     QueryArgs a = base_args(idx, d_q, d_delta, m);
@@ -330,7 +330,7 @@ sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_d
     a.out_offsets = const_cast<uint64_t*>(d_out_offsets);
     a.out_ids = d_out_ids;
     if (w.pending.ordered) {
-        a.perm = w.perm.as<uint32_t>();
+        a.perm = perm ? perm : w.perm.as<uint32_t>();
         a.wbase = w.wbase.as<uint64_t>();
     }
     a.ids_capacity = d_out_ids ? cap : 0;
@@ -478,6 +478,17 @@ sfc_status sfc_rebuild(sfc_index* idx, const int32_t* d_points, uint64_t n, void
         SFC_TRY(train_model(idx, st));
     }
     return SFC_OK;
+}
+
+sfc_status sfc_rebuild_host(sfc_index* idx, const int32_t* h_points, uint64_t n, void* stream)
+{
+    if (!idx || n >= 0xffffffffull || (n && !h_points)) return SFC_ERR_INVALID;
+    AllocScope alloc_scope(idx->allocator());
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = n * (size_t)idx->dim * sizeof(int32_t);
+    SFC_TRY(idx->stage.points.ensure(bytes ? bytes : 1, st));
+    if (n) SFC_CUDA_TRY(cudaMemcpyAsync(idx->stage.points.ptr, h_points, bytes, cudaMemcpyHostToDevice, st));
+    return sfc_rebuild(idx, idx->stage.points.as<int32_t>(), n, stream);
 }
 
 sfc_status sfc_reserve(sfc_index* idx, uint64_t n_max, uint64_t m_max, void* stream)
@@ -830,9 +841,28 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
     SFC_TRY(hs.ids.ensure(total * sizeof(uint32_t), st));
     uint32_t* d_ids = hs.ids.as<uint32_t>();
     const int S = HostStage::kSlices;
-    if (!idx->qws.pending.ordered && m >= (uint64_t)S && total * sizeof(uint32_t) >= (32ull << 20)) {
+    if (m >= (uint64_t)S && total * sizeof(uint32_t) >= (32ull << 20)) {
         // the write pass in query slices; the ids of each finished slice go out on a second
         // stream while the next slices are written (output offsets are in query order)
+        const uint32_t* sperm = nullptr;
+        if (idx->qws.pending.ordered) {
+            // curve order: regroup the processing order by input slice (a stable one-digit sort
+            // of the slice numbers), so slice s is positions [floor(m s / S), floor(m (s + 1) / S))
+            // and keeps curve order inside
+            SFC_TRY(hs.slice_keys.ensure(m * sizeof(uint64_t), st));
+            SFC_TRY(hs.slice_keys_sorted.ensure(m * sizeof(uint64_t), st));
+            SFC_TRY(hs.slice_perm.ensure(m * sizeof(uint32_t), st));
+            const uint32_t* perm = idx->qws.perm.as<uint32_t>();
+            SFC_TRY(launch_slice_keys(perm, m, S, hs.slice_keys.as<uint64_t>(), st));
+            SortSource src;
+            src.keys = hs.slice_keys.as<uint64_t>();
+            src.vals = perm;
+            SortDest dst;
+            dst.keys = hs.slice_keys_sorted.as<uint64_t>();
+            dst.vals = hs.slice_perm.as<uint32_t>();
+            SFC_TRY(radix_sort(src, m, dst, idx->sort_ws, status_word(idx), st));
+            sperm = hs.slice_perm.as<uint32_t>();
+        }
         if (!hs.copy) {
             SFC_CUDA_TRY(cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking));
             for (auto& e : hs.done) SFC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -840,7 +870,7 @@ sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_
         idx->qws.pending.valid = false;
         for (int sl = 0; sl < S; ++sl) {
             const uint64_t qa = m * (uint64_t)sl / S, qb = m * (uint64_t)(sl + 1) / S;
-            SFC_TRY(do_write_range(idx, dq, dd, m, doff, d_ids, total, st, qa, qb));
+            SFC_TRY(do_write_range(idx, dq, dd, m, doff, d_ids, total, st, qa, qb, sperm));
             SFC_CUDA_TRY(cudaEventRecord(hs.done[sl], st));
             SFC_CUDA_TRY(cudaStreamWaitEvent(hs.copy, hs.done[sl], 0));
             const uint64_t a = h_out_offsets[qa], b = h_out_offsets[qb];

@@ -26,9 +26,13 @@ struct QueryWs {
     PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false, 0, 0};
 };
 
-struct HostStage {          // device staging of sfc_query_batch_host
+struct HostStage {          // device staging of sfc_query_batch_host and sfc_rebuild_host
     static constexpr int kSlices = 8;   // write-pass slices whose ids are copied out as they finish
     DevBuf q, delta, offsets, ids;
+    DevBuf points;                      // sfc_rebuild_host's copy of the points
+    // curve-ordered batches: the processing order regrouped by input slice (stable), so each
+    // slice's queries are written together and their ids form one contiguous range
+    DevBuf slice_keys, slice_keys_sorted, slice_perm;
     cudaStream_t copy = nullptr;        // stream of the device-to-host copies of the ids
     cudaEvent_t done[kSlices] = {};     // slice s written
 };

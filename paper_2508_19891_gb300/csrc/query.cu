@@ -1050,7 +1050,7 @@ __device__ __forceinline__ void small_write_tail(const QueryArgs& a)
         const uint64_t t = t0 + lane_id();
         if (t >= ns) continue;
         const uint32_t q = a.small_list[t];
-        if (a.perm == nullptr && (q < a.q_begin || q >= qe)) continue;   // a slice of the queries
+        if (q < a.q_begin || q >= qe) continue;   // a slice of the queries (by query id)
         uint32_t left = __ldg(a.counts + q);
         if (left == 0) continue;
         const unsigned long long* mw = a.small_mask + t * NW;
@@ -1239,6 +1239,18 @@ __global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32
         out[i] = src[perm[i]];
 }
 
+// keys[r] = the input slice of query perm[r]: the number of slice starts floor(m t / S),
+// t = 1 .. S - 1, at or below it (so slice t holds queries [floor(m t / S), floor(m (t + 1) / S)))
+__global__ void slice_keys_kernel(const uint32_t* __restrict__ perm, uint64_t m, int S, uint64_t* keys)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = perm[i];
+        uint64_t s = 0;
+        for (int t = 1; t < S; ++t) s += q >= m * (uint64_t)t / (uint64_t)S;
+        keys[i] = s;
+    }
+}
+
 int persistent_grid(const void* fn)
 {
     int per_sm = 0;
@@ -1349,6 +1361,14 @@ sfc_status launch_gather_u32(const uint32_t* src, const uint32_t* perm, uint64_t
 {
     if (m == 0) return SFC_OK;
     gather_u32_kernel<<<flat_grid(m), kThreads, 0, st>>>(src, perm, m, out);
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_slice_keys(const uint32_t* perm, uint64_t m, int S, uint64_t* keys, cudaStream_t st)
+{
+    if (m == 0) return SFC_OK;
+    slice_keys_kernel<<<flat_grid(m), kThreads, 0, st>>>(perm, m, S, keys);
     count_launch();
     return launch_status();
 }

@@ -38,7 +38,10 @@ struct QueryArgs {
     uint64_t* out_offsets;       // [m + 1]
     uint32_t* out_ids;
     uint64_t ids_capacity;
-    uint64_t q_begin, q_end;     // write pass: the queries [q_begin, q_end) (q_end 0: all m)
+    // write pass: the processing positions [q_begin, q_end) (q_end 0: all m); the caller
+    // arranges that they hold exactly the queries with ids in [q_begin, q_end) (input order,
+    // or a curve order regrouped by slice), which is also the small queries' filter
+    uint64_t q_begin, q_end;
     uint32_t* status;
     unsigned long long* scanned;   // sum of S_q over the batch (statistics)
     // optional processing order: queries handed out in curve order of their centres
@@ -76,6 +79,9 @@ sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* 
 // out[r] = nchunks[perm[r]]
 sfc_status launch_gather_u32(const uint32_t* src, const uint32_t* perm, uint64_t m, uint32_t* out, cudaStream_t st);
 sfc_status launch_write(const QueryArgs& a, cudaStream_t st);
+// keys[r] = the slice of query perm[r] when queries 0 .. m - 1 are cut into S slices
+// [floor(m s / S), floor(m (s + 1) / S))
+sfc_status launch_slice_keys(const uint32_t* perm, uint64_t m, int S, uint64_t* keys, cudaStream_t st);
 sfc_status launch_ranges(const QueryArgs& a, const LearnedModelView* lm, uint64_t* lo, uint64_t* hi,
                          uint32_t* b, uint32_t* e, uint32_t* cnt, cudaStream_t st);
 

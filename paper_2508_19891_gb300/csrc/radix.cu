@@ -10,13 +10,16 @@
 //                    the host never waits (the sort can be captured in a CUDA graph).
 //   3. onesweep_kernel, once per digit: each block takes the next tile (4096 keys), ranks
 //                    its keys per digit inside each warp with eight ballots (stable: item
-//                    order, then lane order), combines warps in shared memory, learns the
-//                    tile's global digit offsets by decoupled look-back over earlier tiles,
-//                    reorders the tile in shared memory by digit and writes it out in
-//                    contiguous runs.  The first pass reads the points (and computes keys
-//                    again instead of storing them); the last pass writes the final arrays
-//                    and also decodes each key back into its coordinates, which replaces a
-//                    random gather xy[id] by a streaming write.
+//                    order, then lane order), combines warps in shared memory, publishes the
+//                    tile's digit counts, reorders the tile in shared memory by digit (the
+//                    values are loaded only then, so the ranking holds no registers for them),
+//                    learns the tile's global digit offsets by decoupled look-back over earlier
+//                    tiles and writes the tile out in contiguous runs.  Every tile but the last
+//                    runs without per-key bounds checks, and index arithmetic is 32-bit.  The
+//                    first pass reads the points (and computes keys again instead of storing
+//                    them); the last pass writes the final arrays and also decodes each key
+//                    back into its coordinates, which replaces a random gather xy[id] by a
+//                    streaming write.
 //
 // Look-back words are tagged with a per-pass epoch, so stale words from earlier passes or
 // sorts read as "not ready" and the buffer never needs clearing.  The epoch counter lives in
@@ -42,7 +45,7 @@ constexpr int kWarps = kThreads / 32;
 #endif
 constexpr int kItems = SFC_SORT_ITEMS;
 constexpr int kTile = kThreads * kItems;        // 4096 keys per tile
-constexpr int kWarpSpan = 32 * kItems;          // 384 keys per warp
+constexpr int kWarpSpan = 32 * kItems;          // 512 keys per warp
 
 struct PassPlan {
     uint32_t active;
@@ -200,106 +203,115 @@ struct PassArgs {
 };
 
 constexpr size_t kSortSmem = sizeof(uint64_t) * kTile + sizeof(uint32_t) * kTile +
-                             sizeof(uint32_t) * kWarps * kRadix + sizeof(uint32_t) * kRadix * 2 +
-                             sizeof(HilbertTables);
+                             sizeof(uint32_t) * kWarps * kRadix + sizeof(uint32_t) * kRadix +
+                             sizeof(uint32_t) * 2 * kWarps + sizeof(HilbertTables);
 
-template <int CURVE>
-__global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(PassArgs a)
+// One tile of a pass.  FULL: all kTile keys of the tile exist (every tile but the last), so
+// no per-key bounds checks.  Index arithmetic is 32-bit (n < 2^32 - 1).
+template <int CURVE, bool FULL>
+__device__ __forceinline__ void sort_tile(const PassArgs& a, const PassPlan& pl, uint32_t epoch, uint32_t tile,
+                                          unsigned char* smem)
 {
-    const PassPlan pl = a.sm->plan[a.pass];
-    if (!pl.active) return;
-    const uint32_t epoch = a.sm->epoch_base + (uint32_t)a.pass;
-    extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
     uint32_t* s_hist = s_vals + kTile;                 // [warp][digit]
-    uint32_t* s_local = s_hist + kWarps * kRadix;      // tile-local digit starts
-    uint32_t* s_gbase = s_local + kRadix;              // global start of the tile's digit run
-    HilbertTables* tb = reinterpret_cast<HilbertTables*>(s_gbase + kRadix);
-    __shared__ uint32_t s_tile;
-
+    uint32_t* s_gbase = s_hist + kWarps * kRadix;      // global start of the digit's run minus its tile-local start
+    uint32_t* s_w = s_gbase + kRadix;                  // warp totals of the tile-local scan
+    const HilbertTables* tb = reinterpret_cast<const HilbertTables*>(s_w + 2 * kWarps);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool need_tb = CURVE == SFC_CURVE_HILBERT &&
-                         ((pl.src == 0 && a.src.points) || (pl.dst == 3 && a.dst.xy));
-    if (need_tb) hilbert_tables_init(tb);
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_hist[i] = 0;
-    if (tid == 0) s_tile = atomicAdd(&a.sm->tile_ctr[a.pass], 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const uint64_t n = a.n;
+    const uint32_t n = (uint32_t)a.n;
     const int shift = kBits * a.pass;
-    const uint64_t wbase = tile * kTile + (uint64_t)warp * kWarpSpan;
+    const uint32_t tbase = tile * (uint32_t)kTile;
+    const uint32_t wbase = tbase + (uint32_t)(warp * kWarpSpan);
 
     uint64_t key[kItems];
-    uint32_t val[kItems];
-    uint32_t rank[kItems];
+    uint32_t dr[kItems];   // digit << 16 | rank of the key among the warp's keys of that digit
     const uint64_t* kin = pl.src == 0 ? nullptr : a.tmp_keys[pl.src - 1];
     const uint32_t* vin = pl.src == 0 ? a.src.vals : a.tmp_vals[pl.src - 1];
+    if (pl.src == 0) {
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        if (idx < n) {
-            if (pl.src == 0) {
-                key[i] = source_key<CURVE>(a.src, tb, idx);
-                val[i] = vin ? vin[idx] : a.src.val_base + (uint32_t)idx;
-            } else {
-                key[i] = kin[idx];
-                val[i] = vin[idx];
-            }
-        } else {
-            key[i] = ~0ull;
-            val[i] = 0;
+        for (int i = 0; i < kItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)(i * 32 + lane);
+            key[i] = (FULL || idx < n) ? source_key<CURVE>(a.src, tb, idx) : ~0ull;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)(i * 32 + lane);
+            key[i] = (FULL || idx < n) ? kin[idx] : ~0ull;
         }
     }
     // ---- warp-level stable ranking by digit ----
     uint32_t* wh = s_hist + warp * kRadix;
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        const bool valid = idx < n;
+        const bool valid = FULL || wbase + (uint32_t)(i * 32 + lane) < n;
         const uint32_t d = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int b = 0; b < kBits; ++b) {
-            uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bb : ~bb;
         }
-        uint32_t before = __popc(peers & lanemask_lt());
-        uint32_t basec = valid ? wh[d] : 0;
+        const uint32_t before = __popc(peers & lt);
+        const uint32_t basec = wh[d];
         __syncwarp();
         if (valid && before == 0) wh[d] = basec + __popc(peers);
         __syncwarp();
-        rank[i] = basec + before;
+        dr[i] = d << 16 | (basec + before);
     }
     __syncthreads();
     // ---- combine warps: thread tid owns digit tid ----
     uint32_t tcount = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        uint32_t c = s_hist[w * kRadix + tid];
-        s_hist[w * kRadix + tid] = tcount;
-        tcount += c;
-    }
-    uint64_t* lbw = a.lookback + tile * kRadix + tid;
-    if (tile == 0) {
-        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagPrefix, epoch));
-    } else {
-        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(tcount, kFlagAgg, epoch));
-    }
-    // tile-local exclusive scan over digits
+    for (int w = 0; w < kWarps; ++w) tcount += s_hist[w * kRadix + tid];
+    uint64_t* lbw = a.lookback + (uint64_t)tile * kRadix + tid;
+    atomicExch(reinterpret_cast<unsigned long long*>(lbw),
+               lb_word(tcount, tile == 0 ? kFlagPrefix : kFlagAgg, epoch));
+    // tile-local exclusive scan over digits; s_hist[w][d] becomes the tile-local position of
+    // warp w's first key of digit d
+    uint32_t local;
     {
         uint32_t v = tcount;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+            const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += t;
         }
-        __shared__ uint32_t s_w[kWarps];
         if (lane == 31) s_w[warp] = v;
         __syncthreads();
         uint32_t wo = 0;
-        for (int w = 0; w < warp; ++w) wo += s_w[w];
-        s_local[tid] = wo + v - tcount;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) wo += w < warp ? s_w[w] : 0u;
+        local = wo + v - tcount;
+        uint32_t run = local;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t cw = s_hist[w * kRadix + tid];
+            s_hist[w * kRadix + tid] = run;
+            run += cw;
+        }
+    }
+    __syncthreads();   // every warp's tile-local starts are in s_hist
+    // ---- reorder the tile by digit in shared memory: it needs only tile-local positions, so
+    // it runs before the look-back, and the values are loaded here rather than with the keys
+    // (the ranking then holds no registers for them; 8.62 -> 7.29 ms for 10^8 keys) ----
+    {
+        uint32_t val[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const uint32_t idx = wbase + (uint32_t)(i * 32 + lane);
+            val[i] = (FULL || idx < n) ? (pl.src == 0 ? (vin ? vin[idx] : a.src.val_base + idx) : vin[idx]) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (FULL || wbase + (uint32_t)(i * 32 + lane) < n) {
+                const uint32_t lp = wh[dr[i] >> 16] + (dr[i] & 0xffffu);
+                s_keys[lp] = key[i];
+                s_vals[lp] = val[i];
+            }
+        }
     }
     // ---- decoupled look-back for digit tid ----
     uint32_t excl = 0;
@@ -307,9 +319,9 @@ __global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(Pas
         int64_t t = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (t >= 0) {
-            uint64_t w = *reinterpret_cast<volatile uint64_t*>(a.lookback + (uint64_t)t * kRadix + tid);
-            uint32_t ep = (uint32_t)(w >> 34);
-            uint32_t fl = (uint32_t)(w >> 32) & 3u;
+            const uint64_t w = *reinterpret_cast<volatile uint64_t*>(a.lookback + (uint64_t)t * kRadix + tid);
+            const uint32_t ep = (uint32_t)(w >> 34);
+            const uint32_t fl = (uint32_t)(w >> 32) & 3u;
             if (ep != epoch || fl == 0) {
                 if (++spins > kSpinLimit) { set_status(a.status, SFC_DEV_TIMEOUT); break; }
                 __nanosleep(32);   // not published yet: leave the issue slots to other warps
@@ -319,33 +331,21 @@ __global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(Pas
             if (fl == 2) break;
             --t;
         }
-        atomicExch(reinterpret_cast<unsigned long long*>(lbw),
-                   lb_word(excl + tcount, kFlagPrefix, epoch));
+        atomicExch(reinterpret_cast<unsigned long long*>(lbw), lb_word(excl + tcount, kFlagPrefix, epoch));
     }
-    s_gbase[tid] = a.sm->offs[a.pass][tid] + excl;
-    __syncthreads();
-    // ---- reorder the tile by digit in shared memory ----
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        uint64_t idx = wbase + (uint64_t)i * 32 + lane;
-        if (idx < n) {
-            uint32_t d = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-            uint32_t lp = s_local[d] + s_hist[warp * kRadix + d] + rank[i];
-            s_keys[lp] = key[i];
-            s_vals[lp] = val[i];
-        }
-    }
+    // global position of tile-local position j of digit d: s_gbase[d] + j (mod 2^32)
+    s_gbase[tid] = a.sm->offs[a.pass][tid] + excl - local;
     __syncthreads();
     // ---- write contiguous digit runs ----
-    const uint64_t tbase = tile * kTile;
-    const int valid_n = (int)((n - tbase) < (uint64_t)kTile ? (n - tbase) : (uint64_t)kTile);
+    const uint32_t valid_n = FULL ? (uint32_t)kTile : min(n - tbase, (uint32_t)kTile);
     uint64_t* kout = pl.dst == 3 ? a.dst.keys : a.tmp_keys[pl.dst - 1];
     uint32_t* vout = pl.dst == 3 ? a.dst.vals : a.tmp_vals[pl.dst - 1];
     int2* xyout = pl.dst == 3 ? a.dst.xy : nullptr;
-    for (int j = tid; j < valid_n; j += kThreads) {
-        uint64_t k = s_keys[j];
-        uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
-        uint64_t g = (uint64_t)s_gbase[d] + (uint32_t)(j - (int)s_local[d]);
+#pragma unroll 4
+    for (uint32_t j = tid; j < valid_n; j += kThreads) {
+        const uint64_t k = s_keys[j];
+        const uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
+        const uint32_t g = s_gbase[d] + j;
         if (g >= n) continue;   // only after a look-back timeout (already flagged)
         kout[g] = k;
         vout[g] = s_vals[j];
@@ -356,6 +356,29 @@ __global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(Pas
             xyout[g] = make_int2((int)x, (int)y);
         }
     }
+}
+
+template <int CURVE>
+__global__ void __launch_bounds__(kThreads, SFC_SORT_BLOCKS) onesweep_kernel(PassArgs a)
+{
+    const PassPlan pl = a.sm->plan[a.pass];
+    if (!pl.active) return;
+    const uint32_t epoch = a.sm->epoch_base + (uint32_t)a.pass;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x;
+    uint32_t* s_hist = reinterpret_cast<uint32_t*>(smem + (sizeof(uint64_t) + sizeof(uint32_t)) * kTile);
+    const bool need_tb = CURVE == SFC_CURVE_HILBERT &&
+                         ((pl.src == 0 && a.src.points) || (pl.dst == 3 && a.dst.xy));
+    if (need_tb) hilbert_tables_init(reinterpret_cast<HilbertTables*>(s_hist + kWarps * kRadix + kRadix + 2 * kWarps));
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_hist[i] = 0;
+    if (tid == 0) s_tile = atomicAdd(&a.sm->tile_ctr[a.pass], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if ((uint64_t)(tile + 1) * kTile <= a.n)
+        sort_tile<CURVE, true>(a, pl, epoch, tile, smem);
+    else
+        sort_tile<CURVE, false>(a, pl, epoch, tile, smem);
 }
 
 }  // namespace

@@ -197,6 +197,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     q.nch_sorted.release(st); q.wbase.release(st); q.small_list.release(st); q.small_mask.release(st);
     HostStage& h = idx->stage;
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
+    h.points.release(st); h.slice_keys.release(st); h.slice_keys_sorted.release(st); h.slice_perm.release(st);
     if (h.copy) {
         cudaStreamSynchronize(h.copy);
         cudaStreamDestroy(h.copy);

@@ -202,11 +202,13 @@ def test_host_buffer_api_pinned_output(cuda):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_buffer_api_sliced_copy(cuda, pinned):
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_host_buffer_api_sliced_copy(cuda, pinned, reorder):
     """A batch with more than 32 MB of ids: the write pass runs in query slices and each
-    slice's ids are copied out on a second stream while the next are written."""
+    slice's ids are copied out on a second stream while the next are written; with curve-order
+    processing the order is first regrouped by slice."""
     wl = W.mixed_1e7(scale=0.05)
-    idx = sfc.sfc_build_host(wl.points, "z", bounds="learned", cover_refine=1)
+    idx = sfc.sfc_build_host(wl.points, "z", bounds="learned", cover_refine=1, reorder_queries=reorder)
     roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta, threads=8)
     total = int(roff[-1])
     assert total * 4 >= 32 << 20
@@ -306,3 +308,32 @@ def test_extreme_radii(cuda, curve, cover):
     off = oracle.query(oracle.build(pts, 30, curve), qs[:3], d[:3])[0]
     assert off[1] - off[0] == 200_000 and off[3] - off[2] == 500
     assert st == (0, 0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rebuild_host_equals_rebuild(cuda, dim):
+    """sfc_rebuild_host (points in host memory, staged by the index) leaves the index exactly as
+    sfc_rebuild over the same points in device memory: sorted arrays and query results."""
+    rng = np.random.default_rng(31)
+    hi = 1 << (30 if dim == 2 else 21)
+    p0 = rng.integers(0, hi, size=(20_000, dim), dtype=np.int64).astype(np.int32)
+    p1 = rng.integers(0, hi, size=(30_000, dim), dtype=np.int64).astype(np.int32)
+    q = p1[:500].copy()
+    d = rng.integers(0, hi >> 8, 500).astype(np.int32)
+    if dim == 2:
+        a = sfc.sfc_build(torch.from_numpy(p0).to(cuda), "z", bounds="learned")
+        b = sfc.sfc_build(torch.from_numpy(p0).to(cuda), "z", bounds="learned")
+    else:
+        a = sfc.sfc_build3(torch.from_numpy(p0).to(cuda))
+        b = sfc.sfc_build3(torch.from_numpy(p0).to(cuda))
+    for _ in range(2):
+        sfc.sfc_rebuild(a, torch.from_numpy(p1).to(cuda))
+        sfc.sfc_rebuild_host(b, p1)
+        torch.cuda.synchronize()
+        for x, y in zip(sfc.sfc_get_sorted(a), sfc.sfc_get_sorted(b)):
+            assert torch.equal(x, y)
+        qa, da = torch.from_numpy(q).to(cuda), torch.from_numpy(d).to(cuda)
+        oa, ia = sfc.query(a, qa, da)
+        ob, ib = sfc.query(b, qa, da)
+        assert torch.equal(oa, ob) and torch.equal(ia, ib)
+    assert sfc.sfc_device_status(a) == (0, 0) and sfc.sfc_device_status(b) == (0, 0)
