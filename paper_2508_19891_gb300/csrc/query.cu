@@ -772,7 +772,7 @@ struct QView {
     int2 q;
     int32_t qz;      // third coordinate of 3-D queries
     int32_t d;       // delta
-    int64_t d2;      // delta^2
+    int64_t d2;      // -(delta^2 + 1): a point is inside iff dx^2 + dy^2 + d2 < 0
 };
 
 // Loads query qi's intervals into the warp's table (lane r takes interval r); every lane calls.
@@ -803,7 +803,7 @@ __device__ __forceinline__ QView load_query(const QueryArgs& a, uint64_t qi, War
         v.qz = 0;
     }
     v.d = __ldg(a.delta + qi);
-    v.d2 = (int64_t)v.d * v.d;
+    v.d2 = -((int64_t)v.d * v.d + 1);
     return v;
 }
 
@@ -836,24 +836,26 @@ struct Geom<kGeomBall3> {
 };
 
 // Exact window tests.  Disc (the problem statement's closed ball): |dx|, |dy| < 2^30, so each
-// square is one signed 32x32 -> 64-bit multiply(-add) and the sum stays below 2^61.  Square
-// (the experiments' windows): max(|dx|, |dy|) <= delta in 32-bit integers.  3-D ball:
-// |dx|, |dy|, |dz| < 2^21, the sum of squares stays below 2^44.
+// square is one signed 32x32 -> 64-bit multiply-add and the sum stays below 2^61; the test
+// dx^2 + dy^2 <= delta^2 is taken as the sign of dx^2 + dy^2 - (delta^2 + 1), read from the
+// high word alone (delta^2 + 1 <= 2^62, so nothing overflows).  Square (the experiments'
+// windows): max(|dx|, |dy|) <= delta in 32-bit integers.  3-D ball: |dx|, |dy|, |dz| < 2^21,
+// the sum of squares stays below 2^44, the same sign test.
 template <int GEOM>
 __device__ __forceinline__ bool is_hit(const QView& v, int2 p)
 {
     const int dx = p.x - v.q.x, dy = p.y - v.q.y;
     if (GEOM == kGeomSquare) return max(abs(dx), abs(dy)) <= v.d;
-    const long long s = (long long)dx * dx + (long long)dy * dy;
-    return s <= v.d2;
+    const long long s = (long long)dx * dx + ((long long)dy * dy + v.d2);
+    return (int)(s >> 32) < 0;
 }
 
 template <int GEOM>
 __device__ __forceinline__ bool is_hit(const QView& v, int4 p)
 {
     const int dx = p.x - v.q.x, dy = p.y - v.q.y, dz = p.z - v.qz;
-    const long long s = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-    return s <= v.d2;
+    const long long s = (long long)dx * dx + ((long long)dy * dy + ((long long)dz * dz + v.d2));
+    return (int)(s >> 32) < 0;
 }
 
 // Filters points [s0, s1) of the query's concatenated intervals; returns the hit count and
@@ -992,7 +994,7 @@ __device__ __forceinline__ QView small_view(const QueryArgs& a, uint64_t qi)
         v.qz = 0;
     }
     v.d = __ldg(a.delta + qi);
-    v.d2 = (int64_t)v.d * v.d;
+    v.d2 = -((int64_t)v.d * v.d + 1);
     return v;
 }
 
@@ -1175,12 +1177,22 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
                     filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words, reinterpret_cast<uint32_t*>(buf));
                     __syncwarp();   // the words are read before buf takes the staged indices
                 }
+                // the WPL groups' popcounts in 16-bit fields of one word, scanned together
+                unsigned long long pk = 0;
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) pk |= (unsigned long long)__popc(words[s]) << (16 * s);
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long t = __shfl_up_sync(0xffffffffu, pk, o);
+                    if (lane >= (unsigned)o) pk += t;
+                }
+                const unsigned long long ktot = __shfl_sync(0xffffffffu, pk, 31);
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
                     const uint32_t wl = words[s];
                     const uint32_t pc = __popc(wl);
-                    const uint32_t incl = warp_incl_scan_u32(pc);
-                    const uint32_t K = __shfl_sync(0xffffffffu, incl, 31);
+                    const uint32_t incl = (uint32_t)(pk >> (16 * s)) & 0xffffu;
+                    const uint32_t K = (uint32_t)(ktot >> (16 * s)) & 0xffffu;
                     if (K == 0) continue;
                     // each lane lists the group-relative indices of its own word's hits
                     uint32_t slot = incl - pc;
