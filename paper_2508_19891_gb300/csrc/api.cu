@@ -196,6 +196,9 @@ sfc_status ensure_query_ws(sfc_index* idx, uint64_t m, cudaStream_t st)
     SFC_TRY(w.ctr.ensure(kCtrWords * sizeof(unsigned long long), st));
     SFC_TRY(w.small_list.ensure(m * sizeof(uint32_t), st));
     SFC_TRY(w.small_mask.ensure(m * kSmallWords * sizeof(unsigned long long), st));
+    SFC_TRY(w.chunk_hits.ensure((kChunkHitsPerQuery * m + 1024) * sizeof(uint32_t), st));
+    SFC_TRY(w.big_items.ensure((kChunkHitsPerQuery * m + 1024) * sizeof(uint32_t), st));
+    SFC_TRY(w.big_list.ensure(m * sizeof(uint32_t), st));
     if (idx->opt.reorder_queries != 0 && idx->dim == 2) {
         SFC_TRY(w.qkeys.ensure(m * sizeof(uint64_t), st));
         SFC_TRY(w.qkeys_sorted.ensure(m * sizeof(uint64_t), st));
@@ -233,6 +236,16 @@ bool use_curve_order(const sfc_index* idx, uint64_t m)
     return idx->n >= (1ull << 24);
 }
 
+// The chunk hit counts of big queries (count pass) and their in-query offsets (write pass).
+void set_big_queries(QueryWs& w, QueryArgs& a)
+{
+    a.chunk_hits = w.chunk_hits.as<uint32_t>();
+    a.big_items = w.big_items.as<uint32_t>();
+    a.big_list = w.big_list.as<uint32_t>();
+    a.big_cap = std::min<uint64_t>(std::min(w.chunk_hits.bytes, w.big_items.bytes) / sizeof(uint32_t), a.mask_chunks);
+    a.big_warps = (uint32_t)num_sms() * 64u * kBigShare;
+}
+
 sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m,
                     uint64_t* d_out_offsets, cudaStream_t st)
 {
@@ -252,6 +265,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     a.masks = w.masks.as<uint32_t>();
     a.chunk = idx->chunk;
     a.mask_chunks = w.masks.bytes / (a.chunk / 8);
+    set_big_queries(w, a);
     a.batch = idx->batch;
     a.qbatch = idx->qbatch;
     a.work_ctr = w.ctr.as<unsigned long long>();
@@ -300,6 +314,7 @@ sfc_status do_count(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, 
     {
         ProfScope ps(idx, "scan", st);
         SFC_TRY(exclusive_scan_u32(a.counts, m, d_out_offsets, idx->scan_ws, a.status, st));
+        SFC_TRY(launch_chunk_prefix(a, st));
     }
     w.pending = {true, d_q, d_delta, m, d_out_offsets, a.chunk, ordered, a.drop, a.norm};
     return SFC_OK;
@@ -322,6 +337,7 @@ sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_d
     a.masks = w.masks.as<uint32_t>();
     a.chunk = w.pending.chunk;
     a.mask_chunks = w.masks.bytes / (a.chunk / 8);
+    set_big_queries(w, a);
     a.batch = idx->batch;
     a.qbatch = idx->qbatch;
     a.work_ctr = w.ctr.as<unsigned long long>();
@@ -338,6 +354,7 @@ sfc_status do_write_range(sfc_index* idx, const int32_t* d_q, const int32_t* d_d
     a.q_end = q_end;
     // the write pass's own work counters start at zero (a repeated write stays correct)
     SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + kCtrWrite, 0, 2 * sizeof(unsigned long long), st));
+    SFC_CUDA_TRY(cudaMemsetAsync(a.work_ctr + kCtrWriteBig, 0, sizeof(unsigned long long), st));
     ProfScope ps(idx, "write", st);
     return launch_write(a, st);
 }

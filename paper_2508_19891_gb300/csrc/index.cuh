@@ -22,6 +22,9 @@ struct PendingCount {       // plan kept between sfc_query_count and sfc_query_w
 struct QueryWs {
     DevBuf ranges, nchunks, chunk_base, counts, masks, ctr;
     DevBuf small_list, small_mask;   // queries of the small-query path and their hit masks
+    DevBuf chunk_hits;               // per-chunk hit counts, then in-query offsets, of big queries
+    DevBuf big_items;                // the chunk slots of big queries, listed query by query
+    DevBuf big_list;                 // the big queries
     DevBuf qkeys, qkeys_sorted, perm, nch_sorted, wbase;   // curve-order processing
     PendingCount pending{false, nullptr, nullptr, 0, nullptr, 0, false, 0, 0};
 };

@@ -453,17 +453,27 @@ __device__ __forceinline__ void for_each_endpoint(const uint64_t* col, int strid
     }
 }
 
-// Lists query i as small (it scans at most kSmallScan points) for the thread-per-query kernels;
-// one atomic per warp.  Every lane of the warp calls.
-__device__ __forceinline__ void small_append(const QueryArgs& a, bool small, uint64_t i)
+// Appends query i to a list (counter work_ctr[ctr]) where flag is set; one atomic per warp.
+// Every lane of the warp calls.
+__device__ __forceinline__ void list_append(const QueryArgs& a, bool flag, uint64_t i, int ctr, uint32_t* list)
 {
-    const uint32_t mask = __ballot_sync(0xffffffffu, small);
+    const uint32_t mask = __ballot_sync(0xffffffffu, flag);
     if (!mask) return;
     const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(a.work_ctr + kCtrSmallSize, (unsigned long long)__popc(mask));
+    if ((int)lane_id() == leader) base = atomicAdd(a.work_ctr + ctr, (unsigned long long)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (small) a.small_list[base + __popc(mask & lanemask_lt())] = (uint32_t)i;
+    if (flag) list[base + __popc(mask & lanemask_lt())] = (uint32_t)i;
+}
+
+// Lists query i as small (it scans at most kSmallScan points) for the thread-per-query kernels,
+// or as a candidate big query (at least kBigChunks chunks) for the write pass.
+__device__ __forceinline__ void plan_lists(const QueryArgs& a, bool active, uint32_t S, uint64_t i)
+{
+    if (a.small_list) list_append(a, active && S > 0 && S <= kSmallScan, i, kCtrSmallSize, a.small_list);
+    if (a.big_list)
+        list_append(a, active && S > kSmallScan && (uint64_t)S > (kBigChunks - 1) * a.chunk, i, kCtrBigList,
+                    a.big_list);
 }
 
 // Optional outputs of the plan (the ranges export); null in the query path.
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, Bounds::kMinBlocks) plan_kernel(Quer
         }
     }
     const bool small = !EXPORT && a.small_list && active && S > 0 && S <= kSmallScan;
-    if (!EXPORT && a.small_list) small_append(a, small, i);
+    if (!EXPORT) plan_lists(a, active, S, i);
     if (!active) return;
     if (!EXPORT) {
         for (uint32_t k = cnt; k < (uint32_t)K; ++k) rp[k] = make_uint2(0u, 0u);
@@ -734,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 4) plan3_kernel(QueryArgs a, PlanExp
         }
     }
     const bool small = !EXPORT && a.small_list && active && S > 0 && S <= kSmallScan;
-    if (!EXPORT && a.small_list) small_append(a, small, i);
+    if (!EXPORT) plan_lists(a, active, S, i);
     if (!active) return;
     if (!EXPORT) {
         uint2* rp = reinterpret_cast<uint2*>(a.ranges + (uint64_t)2 * kCells3 * i);
@@ -1074,6 +1084,14 @@ __device__ __forceinline__ void small_write_tail(const QueryArgs& a)
     }
 }
 
+// A query whose chunks are split over warps (see QueryArgs::chunk_hits): one whose chunks
+// outnumber a warp's share of the batch's G chunks (and at least kBigChunks), so that one warp
+// alone would set the write pass's tail.
+__device__ __forceinline__ bool is_big(const QueryArgs& a, uint64_t G, uint64_t cb, uint64_t nch)
+{
+    return a.chunk_hits != nullptr && nch >= max(kBigChunks, G / a.big_warps) && cb + nch <= a.big_cap;
+}
+
 // ------------------------------------------------------------------------------------
 // count_kernel
 // ------------------------------------------------------------------------------------
@@ -1129,6 +1147,132 @@ __global__ void __launch_bounds__(kThreads) count_kernel(QueryArgs a)
 // ------------------------------------------------------------------------------------
 // write_kernel
 // ------------------------------------------------------------------------------------
+// Writes the ids of one chunk (points [s0, s1) of the query's concatenated intervals, mask slot
+// g) to out_ids[dst ...]; returns the number written.  cr / shift / end: the lane's interval
+// cursor, which only moves forward while the chunks of one query are taken in order.
+template <int WPL, int GEOM>
+__device__ __forceinline__ uint32_t write_chunk(const QueryArgs& a, const QView& v, const WarpTab* tab, uint16_t* buf,
+                                                uint64_t g, uint32_t s0, uint32_t s1, uint64_t dst,
+                                                uint32_t& cr, uint32_t& shift, uint32_t& end)
+{
+    const unsigned lane = lane_id();
+    const uint32_t nw = (s1 - s0 + 31) >> 5;
+    uint32_t words[WPL];
+    if (g < a.mask_chunks) {
+        const uint32_t* mp = a.masks + g * (a.chunk >> 5);
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) {
+            const uint32_t wi = s * 32 + lane;
+            words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
+        }
+    } else {
+        filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words, reinterpret_cast<uint32_t*>(buf));
+        __syncwarp();   // the words are read before buf takes the staged indices
+    }
+    // the WPL groups' popcounts in 16-bit fields of one word, scanned together
+    unsigned long long pk = 0;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) pk |= (unsigned long long)__popc(words[s]) << (16 * s);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, pk, o);
+        if (lane >= (unsigned)o) pk += t;
+    }
+    const unsigned long long ktot = __shfl_sync(0xffffffffu, pk, 31);
+    uint32_t rank = 0;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+        const uint32_t wl = words[s];
+        const uint32_t pc = __popc(wl);
+        const uint32_t incl = (uint32_t)(pk >> (16 * s)) & 0xffffu;
+        const uint32_t K = (uint32_t)(ktot >> (16 * s)) & 0xffffu;
+        if (K == 0) continue;
+        // each lane lists the group-relative indices of its own word's hits
+        uint32_t slot = incl - pc;
+        uint32_t bits = wl;
+        const uint32_t rbase = lane * 32u;
+        while (bits) {
+            buf[slot++] = (uint16_t)(rbase + (uint32_t)(__ffs(bits) - 1));
+            bits &= bits - 1;
+        }
+        __syncwarp();
+        // coalesced gather of the ids and write of the output; a lane's indices grow with t,
+        // so its interval cursor only moves forward
+        const uint32_t gbase = s0 + (uint32_t)s * 1024u;
+        const uint64_t dst0 = dst + rank;
+        if (dst0 + K <= a.ids_capacity) {   // the whole group fits: no per-id check
+            uint32_t* __restrict__ out = a.out_ids + dst0;
+#pragma unroll 4
+            for (uint32_t t = lane; t < K; t += 32) {
+                const uint32_t f = gbase + buf[t];
+                if (f >= end) seek(tab, v.nint, f, cr, shift, end);
+                __stcs(out + t, __ldg(a.ids + (f + shift)));   // written once, not re-read
+            }
+        } else {
+            for (uint32_t t = lane; t < K; t += 32) {
+                const uint32_t f = gbase + buf[t];
+                if (f >= end) seek(tab, v.nint, f, cr, shift, end);
+                const uint64_t d = dst0 + t;
+                if (d < a.ids_capacity) a.out_ids[d] = __ldg(a.ids + (f + shift));
+            }
+        }
+        __syncwarp();
+        rank += K;
+    }
+    return rank;
+}
+
+
+// The chunks of big queries, in batches from the list of their chunk slots (a query's chunks
+// are listed together); a chunk's output position is its query's offset plus the hits of the
+// query's earlier chunks.  Launched before write_kernel, which skips these queries.
+template <int WPL, int GEOM>
+__global__ void __launch_bounds__(kThreads, 8) write_big_kernel(QueryArgs a)
+{
+    // per-warp staging of one group of 32 mask words (<= 1024 hits): each hit's index within
+    // the group's 1024 points, 16 bits; its array position is resolved in the copy loop
+    __shared__ __align__(16) uint16_t s_rel[kThreads / 32][1024];
+    __shared__ WarpTab s_tab[kThreads / 32];
+    uint16_t* buf = s_rel[threadIdx.x >> 5];
+    WarpTab* tab = &s_tab[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const uint64_t qe = a.q_end ? a.q_end : a.m;
+    {
+        const uint64_t total = a.work_ctr[kCtrBigItems];
+        uint64_t q = 0, cb = 0, ce = 0, off = 0;
+        uint32_t k = 0, cr = 0, shift = 0, end = 0;
+        QView v;
+        while (true) {
+            uint64_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(a.work_ctr + kCtrWriteBig, (unsigned long long)a.batch);
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (b0 >= total) break;
+            const uint64_t b1 = min(total, b0 + a.batch);
+            for (uint64_t b = b0; b < b1; ++b) {
+                const uint64_t g = __ldg(a.big_items + b);
+                if (g < cb || g >= ce) {   // a new query: its table, offset and cursor
+                    q = owner_query(a.chunk_base, a.m, g);
+                    cb = __ldg(a.chunk_base + q);
+                    ce = __ldg(a.chunk_base + q + 1);
+                    v = load_query(a, q, tab);
+                    off = a.out_offsets[q];
+                    k = __ldg(a.counts + q);
+                    cr = 0;
+                    shift = 0;
+                    end = 0;
+                }
+                if (q < a.q_begin || q >= qe) continue;
+                const uint64_t j = g - cb;
+                const uint32_t before = __ldg(a.chunk_hits + g);
+                const uint32_t after = g + 1 < ce ? __ldg(a.chunk_hits + g + 1) : k;
+                if (after == before) continue;   // no hits in this chunk
+                const uint32_t s0 = (uint32_t)j * a.chunk;
+                write_chunk<WPL, GEOM>(a, v, tab, buf, g, s0, min(v.S, s0 + a.chunk), off + before, cr, shift, end);
+            }
+        }
+    }
+}
+
 template <int WPL, int GEOM>
 __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
 {
@@ -1141,8 +1285,10 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
     const unsigned lane = lane_id();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.out_offsets[a.m] > a.ids_capacity)
         set_status(a.status, SFC_DEV_CAPACITY);
-    const uint32_t W = a.chunk >> 5;
     const uint64_t qe = a.q_end ? a.q_end : a.m;
+    const uint64_t G = a.chunk_hits ? a.chunk_base[a.m] : 0;
+    // the queries that are not big (write_big_kernel takes those), one warp each, from a
+    // query queue
     while (true) {
         uint64_t q0 = 0;
         if (lane == 0) q0 = atomicAdd(a.work_ctr + kCtrWrite, (unsigned long long)a.qbatch);
@@ -1155,81 +1301,78 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
             const uint64_t cb = __ldg(a.chunk_base + q);
             const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
             if (k == 0 || nch == 0) continue;   // no hits, or a query of the small-query path
+            if (is_big(a, G, cb, nch)) continue;  // written by write_big_kernel
             const QView v = load_query(a, q, tab);
             uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
             uint32_t shift = 0, end = 0;
             const uint64_t off = a.out_offsets[q];
             uint32_t rank = 0;
             for (uint64_t j = 0; j < nch && rank < k; ++j) {
-                const uint64_t g = cb + j;
                 const uint32_t s0 = (uint32_t)j * a.chunk;
-                const uint32_t s1 = min(v.S, s0 + a.chunk);
-                const uint32_t nw = (s1 - s0 + 31) >> 5;
-                uint32_t words[WPL];
-                if (g < a.mask_chunks) {
-                    const uint32_t* mp = a.masks + g * W;
-#pragma unroll
-                    for (int s = 0; s < WPL; ++s) {
-                        const uint32_t wi = s * 32 + lane;
-                        words[s] = wi < nw ? __ldcs(mp + wi) : 0u;
-                    }
-                } else {
-                    filter_chunk<WPL, GEOM>(a, v, tab, s0, s1, words, reinterpret_cast<uint32_t*>(buf));
-                    __syncwarp();   // the words are read before buf takes the staged indices
-                }
-                // the WPL groups' popcounts in 16-bit fields of one word, scanned together
-                unsigned long long pk = 0;
-#pragma unroll
-                for (int s = 0; s < WPL; ++s) pk |= (unsigned long long)__popc(words[s]) << (16 * s);
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned long long t = __shfl_up_sync(0xffffffffu, pk, o);
-                    if (lane >= (unsigned)o) pk += t;
-                }
-                const unsigned long long ktot = __shfl_sync(0xffffffffu, pk, 31);
-#pragma unroll
-                for (int s = 0; s < WPL; ++s) {
-                    const uint32_t wl = words[s];
-                    const uint32_t pc = __popc(wl);
-                    const uint32_t incl = (uint32_t)(pk >> (16 * s)) & 0xffffu;
-                    const uint32_t K = (uint32_t)(ktot >> (16 * s)) & 0xffffu;
-                    if (K == 0) continue;
-                    // each lane lists the group-relative indices of its own word's hits
-                    uint32_t slot = incl - pc;
-                    uint32_t bits = wl;
-                    const uint32_t rbase = lane * 32u;
-                    while (bits) {
-                        buf[slot++] = (uint16_t)(rbase + (uint32_t)(__ffs(bits) - 1));
-                        bits &= bits - 1;
-                    }
-                    __syncwarp();
-                    // coalesced gather of the ids and write of the output; a lane's indices
-                    // grow with t, so its interval cursor only moves forward
-                    const uint32_t gbase = s0 + (uint32_t)s * 1024u;
-                    const uint64_t dst0 = off + rank;
-                    if (dst0 + K <= a.ids_capacity) {   // the whole group fits: no per-id check
-                        uint32_t* __restrict__ out = a.out_ids + dst0;
-#pragma unroll 4
-                        for (uint32_t t = lane; t < K; t += 32) {
-                            const uint32_t f = gbase + buf[t];
-                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
-                            __stcs(out + t, __ldg(a.ids + (f + shift)));   // written once, not re-read
-                        }
-                    } else {
-                        for (uint32_t t = lane; t < K; t += 32) {
-                            const uint32_t f = gbase + buf[t];
-                            if (f >= end) seek(tab, v.nint, f, cr, shift, end);
-                            const uint64_t dst = dst0 + t;
-                            if (dst < a.ids_capacity) a.out_ids[dst] = __ldg(a.ids + (f + shift));
-                        }
-                    }
-                    __syncwarp();
-                    rank += K;
-                }
+                rank += write_chunk<WPL, GEOM>(a, v, tab, buf, cb + j, s0, min(v.S, s0 + a.chunk), off + rank, cr,
+                                               shift, end);
             }
         }
     }
+    // then the small queries
     if (a.small_list) small_write_tail(a);
+}
+
+// Per listed query that is big (one warp each): each chunk's hit count from its mask words
+// (the count pass's ballots), then chunk_hits[cb .. cb + nch) <- their exclusive scan, and the
+// slots cb .. cb + nch - 1 appended to big_items.  The plan listed the queries of at least
+// kBigChunks chunks in its processing order, so the big chunks come out close to curve order
+// and the write pass's gathers of neighbouring big queries share the cache.
+__global__ void chunk_prefix_kernel(QueryArgs a)
+{
+    const unsigned lane = lane_id();
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t nbig = a.work_ctr[kCtrBigList];
+    const uint64_t G = a.chunk_base[a.m];
+    const uint32_t W = a.chunk >> 5;   // mask words per chunk
+    for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nbig; i += warps) {
+        const uint64_t q = a.big_list[i];
+        const uint64_t cb = __ldg(a.chunk_base + q), nch = __ldg(a.chunk_base + q + 1) - cb;
+        if (!is_big(a, G, cb, nch)) continue;
+        // the query's scan length S (its interval lengths), for the last chunk's valid words
+        uint32_t len = 0;
+        if (lane < a.kint) {
+            const uint2 r = __ldg(reinterpret_cast<const uint2*>(a.ranges) + q * a.kint + lane);
+            len = r.y - r.x;
+        }
+        const uint32_t S = __reduce_add_sync(0xffffffffu, len);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.work_ctr + kCtrBigItems, (unsigned long long)nch);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        // 32 chunks at a time, one per lane: its hit count from its mask words (16-byte loads when
+        // a chunk's W words keep 16-byte alignment, i.e. W % 4 == 0; words past the chunk's
+        // points, in the last chunk, are not the query's), then a scan
+        uint32_t carry = 0;
+        for (uint64_t j0 = 0; j0 < nch; j0 += 32) {
+            const uint64_t j = j0 + lane;
+            uint32_t c = 0;
+            if (j < nch) {
+                const uint64_t g = cb + j;
+                const uint32_t s0 = (uint32_t)j * a.chunk;
+                const uint32_t nw = (min(S, s0 + a.chunk) - s0 + 31) >> 5;
+                if ((W & 3u) == 0) {
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.masks + g * W);
+                    for (uint32_t w = 0; w < nw; w += 4) {
+                        const uint4 x = __ldcs(mp + (w >> 2));
+                        c += __popc(x.x) + (w + 1 < nw ? __popc(x.y) : 0u) + (w + 2 < nw ? __popc(x.z) : 0u) +
+                             (w + 3 < nw ? __popc(x.w) : 0u);
+                    }
+                } else {
+                    const uint32_t* mp = a.masks + g * W;
+                    for (uint32_t w = 0; w < nw; ++w) c += __popc(__ldcs(mp + w));
+                }
+                a.big_items[base + j] = (uint32_t)g;
+            }
+            const uint32_t incl = warp_incl_scan_u32(c);
+            if (j < nch) a.chunk_hits[cb + j] = carry + incl - c;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
 }
 
 __global__ void query_keys_kernel(const int32_t* __restrict__ q, uint64_t m, int curve, uint64_t* keys)
@@ -1278,6 +1421,11 @@ void launch_count_write_geom(const QueryArgs& a, bool write, cudaStream_t st)
         int g = persistent_grid((const void*)count_kernel<WPL, GEOM>);
         count_kernel<WPL, GEOM><<<g, kThreads, 0, st>>>(a);
     } else {
+        if (a.chunk_hits) {
+            int gb = persistent_grid((const void*)write_big_kernel<WPL, GEOM>);
+            write_big_kernel<WPL, GEOM><<<gb, kThreads, 0, st>>>(a);
+            count_launch();
+        }
         int g = persistent_grid((const void*)write_kernel<WPL, GEOM>);
         write_kernel<WPL, GEOM><<<g, kThreads, 0, st>>>(a);
     }
@@ -1381,6 +1529,14 @@ sfc_status launch_slice_keys(const uint32_t* perm, uint64_t m, int S, uint64_t* 
 {
     if (m == 0) return SFC_OK;
     slice_keys_kernel<<<flat_grid(m), kThreads, 0, st>>>(perm, m, S, keys);
+    count_launch();
+    return launch_status();
+}
+
+sfc_status launch_chunk_prefix(const QueryArgs& a, cudaStream_t st)
+{
+    if (a.m == 0 || !a.chunk_hits) return SFC_OK;
+    chunk_prefix_kernel<<<num_sms() * 2, kThreads, 0, st>>>(a);   // a few listed queries
     count_launch();
     return launch_status();
 }

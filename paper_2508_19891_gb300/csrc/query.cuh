@@ -47,6 +47,16 @@ struct QueryArgs {
     // optional processing order: queries handed out in curve order of their centres
     const uint32_t* perm;        // [m] query index at each processing rank (NULL: identity)
     const uint64_t* wbase;       // [m + 1] chunk bases in processing order (NULL: chunk_base)
+    // big queries (more chunks than one warp's share, all below big_cap): the plan lists the
+    // candidates; after the count pass, each chunk's hit count (from its mask words) is scanned
+    // inside each big query into chunk_hits[g] (g = chunk_base[q] + j), the chunk's first output
+    // position within the query, and its chunks are listed in big_items
+    // (work_ctr[kCtrBigItems] of them); the write pass spreads the listed chunks over many warps
+    uint32_t* chunk_hits;
+    uint32_t* big_list;          // [m] the queries of at least kBigChunks chunks (work_ctr[kCtrBigList])
+    uint32_t* big_items;
+    uint64_t big_cap;
+    uint32_t big_warps;          // warps the write pass runs (a query is big past G / big_warps chunks)
     // early-termination bitmap (NULL: off) and the cover statistics
     const uint32_t* occ;
     int occ_depth;
@@ -71,9 +81,26 @@ constexpr uint32_t kSmallScan = 64;
 constexpr uint32_t kSmallWords = (kSmallScan + 63) / 64;
 // work counters of a query batch: the count pass's chunk queue, the write pass's query queue and
 // its small-query queue (adjacent: the write pass clears both), the small-list length, the
-// count pass's small-query queue
+// count pass's small-query queue, the write pass's queue of big-query chunks
 constexpr int kCtrCount = 0, kCtrWrite = 1, kCtrSmallWrite = 2, kCtrSmallSize = 3, kCtrSmallCount = 4;
+constexpr int kCtrWriteBig = 5, kCtrBigItems = 6, kCtrBigList = 7;
 constexpr int kCtrWords = 8;
+// a query of at least max(kBigChunks, G / big_warps) chunks is written chunk by chunk by many
+// warps (one warp would set the write pass's tail: single queries reach 10^6 hits)
+#ifndef SFC_BIG_CHUNKS
+#define SFC_BIG_CHUNKS 8
+#endif
+constexpr uint64_t kBigChunks = SFC_BIG_CHUNKS;
+// ... where big_warps is this many times the warps the write pass runs
+#ifndef SFC_BIG_SHARE
+#define SFC_BIG_SHARE 8
+#endif
+constexpr uint32_t kBigShare = SFC_BIG_SHARE;
+// chunk_hits entries per query of a batch (big_cap = min(this * m + 1024, mask chunks))
+constexpr uint64_t kChunkHitsPerQuery = 4;
+// per big query, chunk_hits[g] <- exclusive scan of the query's chunk hit counts (in place),
+// and its chunk slots appended to big_items
+sfc_status launch_chunk_prefix(const QueryArgs& a, cudaStream_t st);
 // curve key of each query centre (invalid centres sort last) with the query index as value
 sfc_status launch_query_keys(const int32_t* q, uint64_t m, int curve, uint64_t* keys, cudaStream_t st);
 // out[r] = nchunks[perm[r]]

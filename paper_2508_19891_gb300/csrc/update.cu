@@ -195,6 +195,7 @@ void release_index(sfc_index* idx, cudaStream_t st)
     q.counts.release(st); q.masks.release(st); q.ctr.release(st);
     q.qkeys.release(st); q.qkeys_sorted.release(st); q.perm.release(st);
     q.nch_sorted.release(st); q.wbase.release(st); q.small_list.release(st); q.small_mask.release(st);
+    q.chunk_hits.release(st); q.big_items.release(st); q.big_list.release(st);
     HostStage& h = idx->stage;
     h.q.release(st); h.delta.release(st); h.offsets.release(st); h.ids.release(st);
     h.points.release(st); h.slice_keys.release(st); h.slice_keys_sorted.release(st); h.slice_perm.release(st);

@@ -337,3 +337,31 @@ def test_rebuild_host_equals_rebuild(cuda, dim):
         ob, ib = sfc.query(b, qa, da)
         assert torch.equal(oa, ob) and torch.equal(ia, ib)
     assert sfc.sfc_device_status(a) == (0, 0) and sfc.sfc_device_status(b) == (0, 0)
+
+
+@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("chunk", [256, 4096])
+def test_big_queries_split_over_warps(cuda, reorder, chunk):
+    """Queries that scan at least 8 chunks are written chunk by chunk by many warps, each chunk
+    at its query's offset plus the hits of the query's earlier chunks.  A Gaussian cluster with
+    40 discs covering most of it (about 2.6·10^5 hits each) among 20,000 small queries equals the
+    oracle in both processing orders, through the device call and through the host call (whose
+    write pass runs in slices: more than 32 MB of ids)."""
+    rng = np.random.default_rng(41)
+    c = rng.normal(1 << 29, 1 << 22, size=(300_000, 2))
+    u = rng.integers(0, 1 << 30, size=(100_000, 2))
+    pts = np.clip(np.concatenate([c, u]), 0, (1 << 30) - 1).astype(np.int32)
+    qs = pts[rng.choice(len(pts), 20_000, replace=False)].copy()
+    d = rng.integers(0, 1 << 16, 20_000).astype(np.int32)
+    qs[:40] = (1 << 29) + rng.integers(-(1 << 20), 1 << 20, size=(40, 2))
+    d[:40] = 1 << 23
+    ref = oracle.build(pts, 30, "z")
+    roff, rids = oracle.query(ref, qs, d, threads=8)
+    assert int(roff[-1]) * 4 >= 32 << 20 and int(np.diff(roff).max()) > 200_000
+    for bounds in ("binary", "learned"):
+        idx, off, ids, st = run_gpu(pts, qs, d, "z", cuda, bounds=bounds, chunk=chunk, reorder_queries=reorder,
+                                    cover_refine=1)
+        assert st == (0, 0)
+        assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+        hoff, hids = sfc.sfc_query_batch_host(idx, qs, d, int(roff[-1]))
+        assert np.array_equal(hoff, roff) and np.array_equal(hids, rids)
