@@ -198,15 +198,18 @@ COUNT_MIN_WARP_INST_PER_32 = 8
 def committed_traffic(kernel: str, workload: str):
     """ncu record of a query kernel at a workload from profiles/traffic.json (DRAM bytes per
     launch and, for the count kernel, warp instructions per scanned point), if it was taken
-    on the current source of the kernel; else None."""
+    on the current source of the kernel (the sha256 of its source files, concatenated in the
+    listed order); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         e = t[kernel]
-        src = os.path.join(ROOT, "paper_2508_19891_gb300", "csrc", e["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != e["source_sha"]:
+        srcs = e["source"] if isinstance(e["source"], list) else [e["source"]]
+        hs = hashlib.sha256()
+        for name in srcs:
+            hs.update(open(os.path.join(ROOT, "paper_2508_19891_gb300", "csrc", name), "rb").read())
+        if hs.hexdigest()[:16] != e["source_sha"]:
             return None
         return e["workloads"][workload]
     except Exception:
@@ -215,8 +218,10 @@ def committed_traffic(kernel: str, workload: str):
 
 def query_rooflines(agg, scanned: int, hits: int, dim: int, hbm_peak: float, peak_kind: str,
                     workload: str = WORKLOAD, sm_count: int = 152, sm_mhz: float = 2070.0):
-    """Roofline objects of the two query kernels (one launch each per step; the small queries
-    run inside them), the one with the longer launch first.
+    """Roofline objects of the two query passes (the small queries run inside them), the one
+    with the longer time first.  The count pass is one count_kernel launch; the write pass is
+    write_kernel, preceded by write_big_kernel for the chunks of queries split over warps
+    (its time and DRAM bytes are the two launches together).
 
     write_kernel, bound by HBM: the method must read every reported id and write it, 8 B per
     hit (the hit mask is the two-pass implementation's own traffic and is not counted).
@@ -234,6 +239,8 @@ def query_rooflines(agg, scanned: int, hits: int, dim: int, hbm_peak: float, pea
         traffic = rec.get("dram_bytes_per_launch")
         o = {"kernel": name, "avg_launch_ms": avg, "traffic": traffic,
              "traffic_source": rec.get("command") if traffic is not None else None}
+        if name == "write_kernel":
+            o["launches"] = "write_big_kernel + write_kernel"
         if traffic is not None:
             gbs = traffic / (avg / 1e3) / 1e9
             o.update({"dram_gbs": gbs, "dram_frac": gbs / hbm_peak, "dram_frac_nominal": gbs / NOMINAL_HBM_GBS})

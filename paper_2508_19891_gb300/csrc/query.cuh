@@ -91,9 +91,12 @@ constexpr int kCtrWords = 8;
 #define SFC_BIG_CHUNKS 8
 #endif
 constexpr uint64_t kBigChunks = SFC_BIG_CHUNKS;
-// ... where big_warps is this many times the warps the write pass runs
+// ... where big_warps is this many times the warps the write pass runs: a query is split once
+// it has more than a quarter of one warp's share of the chunks.  Measured: splitting from 8
+// chunks keeps dynamic-5e7's write pass at 1.6-2.1 ms (2.7-16 ms unsplit), while splitting
+// mixed-1e7's queries of 8-20 chunks costs 0.17 ms there (1.14 -> 1.31 ms).
 #ifndef SFC_BIG_SHARE
-#define SFC_BIG_SHARE 8
+#define SFC_BIG_SHARE 4
 #endif
 constexpr uint32_t kBigShare = SFC_BIG_SHARE;
 // chunk_hits entries per query of a batch (big_cap = min(this * m + 1024, mask chunks))

@@ -72,6 +72,24 @@ def test_record_only_for_the_measured_source_and_workload(tmp_path, monkeypatch)
     assert bench.committed_traffic("write_kernel", "w1") is None     # source changed since
 
 
+def test_record_hashes_every_listed_source(tmp_path, monkeypatch):
+    """A record taken on two source files (the kernels and their header) holds only while
+    neither changes."""
+    src_dir = tmp_path / "paper_2508_19891_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (src_dir / "query.cu").write_text("// kernels\n")
+    (src_dir / "query.cuh").write_text("// constants\n")
+    sha = hashlib.sha256(b"// kernels\n// constants\n").hexdigest()[:16]
+    rec = {"write_kernel": {"source": ["query.cu", "query.cuh"], "source_sha": sha,
+                            "workloads": {"w1": {"dram_bytes_per_launch": 5}}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.committed_traffic("write_kernel", "w1")["dram_bytes_per_launch"] == 5
+    (src_dir / "query.cuh").write_text("// constants, changed\n")
+    assert bench.committed_traffic("write_kernel", "w1") is None
+
+
 def test_committed_record_has_both_query_kernels():
     """The committed record covers both query kernels, each with its source and the ncu
     command of every workload it holds."""
@@ -79,7 +97,7 @@ def test_committed_record_has_both_query_kernels():
         rec = json.load(f)
     for k in ("count_kernel", "write_kernel"):
         e = rec[k]
-        assert e["source"] == "query.cu" and len(e["source_sha"]) == 16
+        assert e["source"] == ["query.cu", "query.cuh"] and len(e["source_sha"]) == 16
         assert e["workloads"]
         for w, r in e["workloads"].items():
             assert w in bench.WORKLOADS
