@@ -445,6 +445,9 @@ class StaticBench:
             "reported_pts_per_s_query_phase": H / (query_ms / 1e3),
             "hits_per_step": H, "scanned_per_step": S, "chunks": stats["chunks"],
             "scan_amplification": S / max(H, 1),
+            # coordinates of every scanned point plus the read and write of every reported id,
+            # over the query phase; above the DRAM rate where overlapping queries share L2
+            "algorithmic_gbs_query_phase": (4 * self.dim * S + 8 * H) / (query_ms / 1e3) / 1e9,
             "cover_cells": cell_stats["cells"], "cells_found_empty": cell_stats["empty"],
         })
         return out
