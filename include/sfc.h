@@ -242,8 +242,10 @@ sfc_status sfc_query_batch(sfc_index* idx, const int32_t* d_q, const int32_t* d_
 
 /* Whole query batch with host buffers: copies h_q/h_delta in, runs the batch, copies
  * h_out_offsets (uint64[m+1]) and the ids back (staged in device memory; page-locked host
- * buffers copy fastest).  Synchronises `stream`.  If the total exceeds ids_capacity, only h_out_offsets is
- * written and SFC_ERR_CAPACITY is returned. */
+ * buffers copy fastest).  Past 32 MB of ids the write pass runs in 8 slices of the queries (by
+ * input index) and each slice's ids go out on a second stream while the next slices are written.
+ * Synchronises `stream`.  If the total exceeds ids_capacity, only h_out_offsets is written and
+ * SFC_ERR_CAPACITY is returned. */
 sfc_status sfc_query_batch_host(sfc_index* idx, const int32_t* h_q, const int32_t* h_delta,
                                 uint64_t m, uint64_t* h_out_offsets, uint32_t* h_out_ids,
                                 uint64_t ids_capacity, void* stream);
