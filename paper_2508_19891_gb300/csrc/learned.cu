@@ -568,12 +568,11 @@ __device__ int2 block_minmax_i(int lo, int hi, int* sh)
 }
 
 // One block per leaf j, over its positions [bound[j], bound[j + 1]):
-//   the least-squares line of position against key offset (v = position - first against
-//   u = key - base, base the leaf's smallest key; fp32 with the mean taken first and
-//   fixed-order reductions), then the exact error window: min and max of
-//   (position - prediction) over the leaf's keys with the query-time fp32 predict function,
-//   then its coarse and fine fences.  The leaf's keys are read three times; the later reads
-//   mostly come from L2.
+//   its coarse and fine fences, then the least-squares line of position against key offset
+//   (v = position - first against u = key - base, base the leaf's smallest key; fp32 sums of
+//   u shifted by the fence keys' mean, fixed-order reductions), then the exact error window:
+//   min and max of (position - prediction) over the leaf's keys with the query-time fp32
+//   predict function.  The leaf's keys are read twice; the second read mostly comes from L2.
 // Threads per leaf block: at 10^8 keys (about 24,000 per leaf) 512 threads take the stage from
 // 1.26 ms (256 threads) to 0.99 ms; 1,024 gain another 2%.
 #ifndef SFC_LEAF_THREADS
@@ -600,41 +599,46 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_stage_kernel(const uint64_t
     const uint32_t cnt = lp.end - lp.first;
     const uint64_t* kp = keys + lp.first;
     const uint32_t B = blockDim.x;
+    // the fences first: 256 keys at evenly spaced positions of the leaf, whose mean is the shift
+    // of the one-pass sums below (close to the leaf's mean, so the variance keeps its precision)
+    float sf = 0.0f;
+    for (uint32_t r = threadIdx.x; r < (uint32_t)kFenceFine; r += B) {
+        const uint64_t k = cnt ? __ldg(kp + ((uint64_t)r * cnt) / kFenceFine) : ~0ull;
+        fence_fine[(size_t)j * kFenceFine + r] = k;
+        if (r % kFence == 0) fence[(size_t)j * kFence + r / kFence] = k;
+        if (cnt) sf += __ull2float_rn(k - lp.base);
+    }
     if (cnt >= 2) {
-        // two passes (the mean first, for fp32 accuracy); each thread keeps four loads in flight
-        float su = 0.0f;
-        for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
-            float u[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t i = i0 + q * B;
-                u[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) : 0.0f;
-            }
-            su += (u[0] + u[1]) + (u[2] + u[3]);
-        }
-        const float mu = block_sum_f(su, sh) / (float)cnt;
+        // one pass over d = u - mu0 (u = key - base): sum d, sum d^2 and sum d (i - mean i);
+        // each thread keeps four loads in flight
+        const float mu0 = block_sum_f(sf, sh) / (float)kFenceFine;
         const float mv = 0.5f * (float)(cnt - 1);   // mean of 0 .. cnt - 1
-        float sxy = 0.0f, sxx = 0.0f;
+        float s1 = 0.0f, sdd = 0.0f, sdi = 0.0f;
         for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += 4 * B) {
-            float du[4];
+            float d[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint32_t i = i0 + q * B;
-                du[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) - mu : 0.0f;
+                d[q] = i < cnt ? __ull2float_rn(__ldg(kp + i) - lp.base) - mu0 : 0.0f;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint32_t i = i0 + q * B;
                 if (i < cnt) {
-                    sxy = fmaf(du[q], (float)i - mv, sxy);
-                    sxx = fmaf(du[q], du[q], sxx);
+                    s1 += d[q];
+                    sdd = fmaf(d[q], d[q], sdd);
+                    sdi = fmaf(d[q], (float)i - mv, sdi);
                 }
             }
         }
-        sxy = block_sum_f(sxy, sh);
-        sxx = block_sum_f(sxx, sh);
-        lp.slope = sxx > 0.0f ? sxy / sxx : 0.0f;
-        lp.icpt = mv - lp.slope * mu;
+        s1 = block_sum_f(s1, sh);
+        sdd = block_sum_f(sdd, sh);
+        sdi = block_sum_f(sdi, sh);
+        // sum (i - mean i) = 0, so sdi is already the centred cross sum
+        const float dbar = s1 / (float)cnt;
+        const float sxx = sdd - (float)cnt * dbar * dbar;
+        lp.slope = sxx > 0.0f ? sdi / sxx : 0.0f;
+        lp.icpt = mv - lp.slope * (mu0 + dbar);
     }
     if (cnt >= 1) {
         int lo = 0x7fffffff, hi = (int)0x80000000;
@@ -647,11 +651,6 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_stage_kernel(const uint64_t
         const int2 w = block_minmax_i(lo, hi, shi);
         lp.err_lo = w.x;
         lp.err_hi = w.y;
-    }
-    for (uint32_t r = threadIdx.x; r < (uint32_t)kFenceFine; r += B) {
-        const uint64_t k = cnt ? __ldg(kp + ((uint64_t)r * cnt) / kFenceFine) : ~0ull;
-        fence_fine[(size_t)j * kFenceFine + r] = k;
-        if (r % kFence == 0) fence[(size_t)j * kFence + r / kFence] = k;
     }
     if (threadIdx.x == 0) leaf[j] = lp;
 }
