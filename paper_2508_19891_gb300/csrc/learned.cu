@@ -16,11 +16,11 @@
 //                        one binary search per leaf boundary over the sorted keys (routing
 //                        the probed keys) instead of routing every key; bound_max_kernel
 //                        keeps the boundaries in order
-//   leaf_stage_kernel    one block per leaf: least-squares line of position against key
-//                        offset (two passes, fp32 with the mean taken first), the exact
+//   leaf_stage_kernel    one block per leaf: the leaf's coarse (16) and fine (256) fences,
+//                        the least-squares line of position against key offset (one pass of
+//                        fp32 sums shifted by the fine fence's mean), and the exact
 //                        min / max of (position - prediction) over the leaf's keys with the
-//                        same fp32 predict function the queries call, and the leaf's coarse
-//                        (16) and fine (256) fences
+//                        same fp32 predict function the queries call
 #include <algorithm>
 #include <cmath>
 #include <cstring>
