@@ -153,3 +153,22 @@ def test_rejections(cuda):
     bad = to_dev(np.array([[0, 0, S3]], np.int32), cuda)
     idx2 = sfc.sfc_build3(bad)
     assert sfc.sfc_device_status(idx2)[1] & sfc.SFC_DEV_BAD_POINT
+
+
+def test_big_balls_split_over_warps(cuda):
+    """3-D queries of many chunks are written chunk by chunk by many warps: a dense Gaussian
+    cloud with 20 balls covering most of it among small ones equals the oracle, with chunks of
+    32 points (the chunk hit counts then come from one mask word per chunk) and of 4096."""
+    rng = np.random.default_rng(43)
+    c = rng.normal(1 << 20, 1 << 14, size=(150_000, 3))
+    u = rng.integers(0, 1 << 21, size=(50_000, 3))
+    p = np.clip(np.concatenate([c, u]), 0, (1 << 21) - 1).astype(np.int32)
+    qs = p[rng.choice(len(p), 5_000, replace=False)].copy()
+    d = rng.integers(0, 1 << 9, 5_000).astype(np.int32)
+    qs[:20] = (1 << 20) + rng.integers(-(1 << 12), 1 << 12, size=(20, 3))
+    d[:20] = 1 << 15
+    for chunk in (32, 4096):
+        idx = sfc.sfc_build3(to_dev(p, cuda), chunk=chunk, cover_refine=1)
+        off, _ = _same(idx, p, qs, d, cuda)
+        assert int(np.diff(u64(off)).max()) > 50_000
+        assert sfc.sfc_device_status(idx) == (0, 0)

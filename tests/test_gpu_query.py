@@ -365,3 +365,20 @@ def test_big_queries_split_over_warps(cuda, reorder, chunk):
         assert np.array_equal(off, roff) and np.array_equal(ids, rids)
         hoff, hids = sfc.sfc_query_batch_host(idx, qs, d, int(roff[-1]))
         assert np.array_equal(hoff, roff) and np.array_equal(hids, rids)
+
+
+def test_big_queries_with_small_mask_budget(cuda):
+    """With a 1 MB hit-mask budget only the big queries whose chunks all have mask slots are
+    split over warps; the others, and the chunks past the budget, are re-filtered by the query
+    walk.  Results equal the oracle for chunk sizes that do and do not keep 16-byte mask rows."""
+    rng = np.random.default_rng(47)
+    c = rng.normal(1 << 29, 1 << 22, size=(200_000, 2))
+    pts = np.clip(c, 0, (1 << 30) - 1).astype(np.int32)
+    qs = pts[rng.choice(len(pts), 5_000, replace=False)].copy()
+    d = rng.integers(0, 1 << 15, 5_000).astype(np.int32)
+    qs[:30] = (1 << 29) + rng.integers(-(1 << 21), 1 << 21, size=(30, 2))
+    d[:30] = 1 << 23
+    for chunk in (96, 256):
+        idx, st = assert_same(pts, qs, d, "z", cuda, chunk=chunk, mask_budget_mb=1, cover_refine=1,
+                              reorder_queries=1)
+        assert st == (0, 0)
