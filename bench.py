@@ -76,6 +76,10 @@ def parse(argv=None):
     ap.add_argument("--m", type=float, default=1e6, help="paper-*: queries (uniformly placed)")
     ap.add_argument("--cover", type=int, choices=[-1, 0, 1, 2], default=-1,
                     help="cover of each query's ball: 0 cells(Q), 1/2 levels finer, -1 autotuned")
+    ap.add_argument("--tuning", default=None, metavar="CHUNK,BATCH,QBATCH",
+                    help="set the scan settings instead of autotuning them (with --cover 0/1/2): "
+                         "replays a plain run's choice under a profiler, whose overhead would "
+                         "change the autotuner's timings")
     ap.add_argument("--repeats", type=int, default=10,
                     help="interleaved repeats of the learned / binary / untrained query-phase comparison")
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
@@ -371,7 +375,15 @@ class StaticBench:
         # size the output once (the total is the same for every step) and let the autotuner
         # pick the cover, the scan's chunk size and work-queue batches for this shape
         self.ix = sfc.sfc_build3(self.pts, **opts) if self.dim == 3 else sfc.sfc_build(self.pts, self.curve, **opts)
-        self.tuned = sfc.sfc_autotune(self.ix, self.q, self.d)
+        if args.tuning:
+            if args.cover < 0:
+                raise SystemExit("--tuning needs --cover 0, 1 or 2")
+            chunk, batch, qbatch = (int(x) for x in args.tuning.split(","))
+            sfc.sfc_set_tuning(self.ix, chunk, batch, qbatch)
+            self.tuned = {"chunk": chunk, "batch": batch, "qbatch": qbatch, "cover": sfc.sfc_cover_refine(self.ix),
+                          "pinned": True}
+        else:
+            self.tuned = sfc.sfc_autotune(self.ix, self.q, self.d)
         off, ids = sfc.query(self.ix, self.q, self.d)
         self.total = int(off[-1].item())
         del off, ids
@@ -380,6 +392,14 @@ class StaticBench:
         self.g = None
         if self.graph:
             self.g = sfc.sfc_graph_capture(self.ix, self.pts, self.q, self.d, self.off, self.ids, self.total)
+
+    def same_tuning(self, ix):
+        """Gives another index of the same shape the scan settings of the timed one: the
+        pinned ones under --tuning, else the autotuner's cached choice."""
+        if self.tuned.get("pinned"):
+            self.sfc.sfc_set_tuning(ix, self.tuned["chunk"], self.tuned["batch"], self.tuned["qbatch"])
+        else:
+            self.sfc.sfc_autotune(ix, self.q, self.d)
 
     def step(self, i):
         sfc = self.sfc
@@ -473,7 +493,7 @@ class StaticBench:
         if self.bounds != "learned":
             sfc.sfc_train_model(self.ix)
         ix0 = sfc.sfc_build(self.pts, self.curve, **{**self.opts, "bounds": "learned", "train_steps": 0})
-        sfc.sfc_autotune(ix0, self.q, self.d)   # same shape and options: the cached choice
+        self.same_tuning(ix0)
         sfc.sfc_set_cover(ix0, sfc.sfc_cover_refine(self.ix))
         modes = [("learned", self.ix, "learned"), ("binary", self.ix, "binary"),
                  ("learned_untrained", ix0, "learned")]
@@ -539,7 +559,7 @@ class StaticBench:
         opts = {**self.opts, "profile": 0}
         build_ms = timed(lambda: sfc.sfc_build(self.pts, "h", **{**opts, "bounds": "binary"}).close(), torch, flush)
         ix = sfc.sfc_build(self.pts, "h", **opts)
-        sfc.sfc_autotune(ix, self.q, self.d)
+        self.same_tuning(ix)
         res = {"build_ms": build_ms, "build_pts_per_s": self.wl.n / (build_ms / 1e3),
                "cover": sfc.sfc_cover_refine(ix)}
         for mode in (["binary", "learned"] if self.bounds == "learned" else ["binary"]):

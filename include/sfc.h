@@ -267,6 +267,14 @@ sfc_status sfc_reserve_queries(sfc_index* idx, uint64_t m, void* stream);
 sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_delta, uint64_t m, int force,
                         int* h_chunk, int* h_batch, int* h_qbatch, void* stream);
 
+/* Sets the three scan settings that sfc_autotune chooses, without timing anything: the chunk
+ * in points (32 ... 4096, a multiple of 32), the chunks per work-queue grab of the count pass
+ * (batch) and the queries per grab of the write pass (qbatch), each 1 ... 1024; otherwise
+ * SFC_ERR_INVALID and nothing changes.  Results do not depend on them, and a count already
+ * made keeps its own chunk for its write.  For replaying a measured choice where timing it
+ * again would give another (under a profiler, whose overhead changes the timings). */
+sfc_status sfc_set_tuning(sfc_index* idx, int chunk, int batch, int qbatch);
+
 /* Chooses the bound search of later queries.  SFC_BOUNDS_LEARNED requires a trained model
  * (sfc_train_model or opt->bounds at build), else SFC_ERR_STATE. */
 sfc_status sfc_set_bounds_mode(sfc_index* idx, sfc_bounds mode);

@@ -164,6 +164,7 @@ def lib():
             "sfc_launch_count": (u64, []),
             "sfc_pool_bytes_in_use": (u64, []),
             "sfc_autotune": (ci, [P, P, P, u64, ci, P, P, P, P]),
+            "sfc_set_tuning": (ci, [P, ci, ci, ci]),
             "sfc_rebuild": (ci, [P, P, u64, P]),
             "sfc_rebuild_host": (ci, [P, P, u64, P]),
             "sfc_reserve": (ci, [P, u64, u64, P]),
@@ -489,6 +490,10 @@ def sfc_autotune(index: Index, q: torch.Tensor, delta: torch.Tensor, force: bool
                               ctypes.byref(b), ctypes.byref(w), _stream(stream)), "sfc_autotune")
     return {"chunk": c.value, "batch": b.value, "qbatch": w.value,
             "cover": int(lib().sfc_cover_refine(index.handle))}
+
+
+def sfc_set_tuning(index: Index, chunk: int, batch: int, qbatch: int):
+    _check(lib().sfc_set_tuning(index.handle, int(chunk), int(batch), int(qbatch)), "sfc_set_tuning")
 
 
 def sfc_reserve_queries(index: Index, m: int, stream=None):

@@ -779,6 +779,17 @@ sfc_status sfc_autotune(sfc_index* idx, const int32_t* d_q, const int32_t* d_del
     return SFC_OK;
 }
 
+sfc_status sfc_set_tuning(sfc_index* idx, int chunk, int batch, int qbatch)
+{
+    if (!idx || chunk < 32 || chunk > 4096 || (chunk & 31) || batch < 1 || batch > 1024 || qbatch < 1 ||
+        qbatch > 1024)
+        return SFC_ERR_INVALID;
+    idx->chunk = (uint32_t)chunk;
+    idx->batch = (uint32_t)batch;
+    idx->qbatch = (uint32_t)qbatch;
+    return SFC_OK;
+}
+
 sfc_status sfc_set_query_norm(sfc_index* idx, sfc_norm norm)
 {
     if (!idx || (norm != SFC_NORM_DISC && norm != SFC_NORM_SQUARE)) return SFC_ERR_INVALID;

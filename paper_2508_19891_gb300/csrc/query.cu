@@ -1273,6 +1273,12 @@ __global__ void __launch_bounds__(kThreads, 8) write_big_kernel(QueryArgs a)
     }
 }
 
+// A hint that starts moving the line holding p into L2; nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int WPL, int GEOM>
 __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
 {
@@ -1287,6 +1293,7 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
         set_status(a.status, SFC_DEV_CAPACITY);
     const uint64_t qe = a.q_end ? a.q_end : a.m;
     const uint64_t G = a.chunk_hits ? a.chunk_base[a.m] : 0;
+    const uint32_t W = a.chunk >> 5;   // mask words per chunk
     // the queries that are not big (write_big_kernel takes those), one warp each, from a
     // query queue
     while (true) {
@@ -1295,22 +1302,44 @@ __global__ void __launch_bounds__(kThreads, 8) write_kernel(QueryArgs a)
         q0 = a.q_begin + __shfl_sync(0xffffffffu, q0, 0);
         if (q0 >= qe) break;
         const uint64_t q1 = min(qe, q0 + a.qbatch);
-        for (uint64_t r = q0; r < q1; ++r) {
-            const uint64_t q = a.perm ? __ldg(a.perm + r) : r;
-            const uint32_t k = __ldg(a.counts + q);
-            const uint64_t cb = __ldg(a.chunk_base + q);
-            const uint64_t nch = __ldg(a.chunk_base + q + 1) - cb;
-            if (k == 0 || nch == 0) continue;   // no hits, or a query of the small-query path
-            if (is_big(a, G, cb, nch)) continue;  // written by write_big_kernel
-            const QView v = load_query(a, q, tab);
-            uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
-            uint32_t shift = 0, end = 0;
-            const uint64_t off = a.out_offsets[q];
-            uint32_t rank = 0;
-            for (uint64_t j = 0; j < nch && rank < k; ++j) {
-                const uint32_t s0 = (uint32_t)j * a.chunk;
-                rank += write_chunk<WPL, GEOM>(a, v, tab, buf, cb + j, s0, min(v.S, s0 + a.chunk), off + rank, cr,
-                                               shift, end);
+        for (uint64_t qs = q0; qs < q1; qs += 32) {
+            const uint32_t nb = (uint32_t)min((uint64_t)32, q1 - qs);
+            // lane i loads query qs + i's bookkeeping and starts its intervals and its first
+            // chunk's mask words towards L2, so that these loads are in flight for the whole
+            // grab together instead of one query after another
+            uint64_t mq = 0, mcb = 0;
+            uint32_t mk = 0, mnch = 0;
+            if (lane < nb) {
+                mq = a.perm ? __ldg(a.perm + qs + lane) : qs + lane;
+                prefetch_l2(reinterpret_cast<const uint2*>(a.ranges) + mq * a.kint);
+                mk = __ldg(a.counts + mq);
+                mcb = __ldg(a.chunk_base + mq);
+                mnch = (uint32_t)(__ldg(a.chunk_base + mq + 1) - mcb);
+                if (mk != 0 && mnch != 0 && mcb < a.mask_chunks) {
+                    // the lines of the first chunk's mask that the query surely uses: all when
+                    // further chunks follow, else the first (its points may end within it, and
+                    // the count pass writes no words past them)
+                    const uint32_t pw = mnch > 1 ? W : min(W, 32u);
+                    for (uint32_t w = 0; w < pw; w += 32) prefetch_l2(a.masks + mcb * W + w);
+                }
+            }
+            for (uint32_t i = 0; i < nb; ++i) {
+                const uint64_t q = __shfl_sync(0xffffffffu, mq, i);
+                const uint32_t k = __shfl_sync(0xffffffffu, mk, i);
+                const uint64_t cb = __shfl_sync(0xffffffffu, mcb, i);
+                const uint32_t nch = __shfl_sync(0xffffffffu, mnch, i);
+                if (k == 0 || nch == 0) continue;   // no hits, or a query of the small-query path
+                if (is_big(a, G, cb, nch)) continue;  // written by write_big_kernel
+                const uint64_t off = a.out_offsets[q];
+                const QView v = load_query(a, q, tab);
+                uint32_t cr = 0;   // this lane's interval cursor (indices only grow within a query)
+                uint32_t shift = 0, end = 0;
+                uint32_t rank = 0;
+                for (uint32_t j = 0; j < nch && rank < k; ++j) {
+                    const uint32_t s0 = j * a.chunk;
+                    rank += write_chunk<WPL, GEOM>(a, v, tab, buf, cb + j, s0, min(v.S, s0 + a.chunk), off + rank,
+                                                   cr, shift, end);
+                }
             }
         }
     }

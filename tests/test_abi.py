@@ -50,6 +50,7 @@ def test_host_only_calls(libsfc):
     assert L.sfc_build(ctypes.byref(h), None, 5, 0, None, None, None) == sfc.SFC_ERR_INVALID
     assert L.sfc_build(ctypes.byref(h), None, 0, 7, None, None, None) == sfc.SFC_ERR_INVALID
     assert L.sfc_query_count(None, None, None, 0, None, None) == sfc.SFC_ERR_INVALID
+    assert L.sfc_set_tuning(None, 1024, 4, 8) == sfc.SFC_ERR_INVALID
     # an allocator must bring both callbacks (checked before any device work)
     half = sfc.sfc_allocator()
     half.alloc = sfc.SFC_ALLOC_FN(lambda n, s, c: None)

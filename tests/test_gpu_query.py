@@ -291,6 +291,26 @@ def test_autotune(cuda):
         sfc.sfc_set_cover(idx3, 3)
 
 
+def test_set_tuning(cuda):
+    """Scan settings set by hand (chunk, count-pass and write-pass grabs), the extremes among
+    them: the answers equal the oracle's under each; values out of range are refused and leave
+    the last valid settings in place."""
+    wl = W.mixed_1e7(scale=0.02)
+    q, d = to_dev(wl.queries, cuda), to_dev(wl.delta, cuda)
+    idx = sfc.sfc_build(to_dev(wl.points, cuda), "z", bounds="learned", cover_refine=1)
+    roff, rids = oracle.query(oracle.build(wl.points), wl.queries, wl.delta)
+    for chunk, batch, qbatch in [(32, 1, 1), (96, 3, 5), (4096, 16, 2), (4096, 1024, 1024)]:
+        sfc.sfc_set_tuning(idx, chunk, batch, qbatch)
+        off, ids = sfc.query(idx, q, d)
+        assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids), (chunk, batch, qbatch)
+    for bad in [(16, 1, 1), (4128, 1, 1), (100, 1, 1), (1024, 0, 1), (1024, 1, 0), (1024, 1025, 1),
+                (1024, 1, 1025)]:
+        with pytest.raises(sfc.SfcError):
+            sfc.sfc_set_tuning(idx, *bad)
+    off, ids = sfc.query(idx, q, d)   # the last valid settings are still in place
+    assert np.array_equal(u64(off), roff) and np.array_equal(u32(ids), rids)
+
+
 @pytest.mark.parametrize("curve", ["z", "h"])
 @pytest.mark.parametrize("cover", [0, 2])
 def test_extreme_radii(cuda, curve, cover):
