@@ -85,7 +85,25 @@ def parse(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    pinned_tuning(args)   # refuse a malformed --tuning before any work
+    return args
+
+
+def pinned_tuning(args):
+    """The scan settings given with --tuning as (chunk, batch, qbatch), else None.  They replace
+    the autotuner's timed choice, which also picks the cover, so they need an explicit --cover;
+    the dynamic workload tunes its own index and takes none."""
+    if not args.tuning:
+        return None
+    if args.workload == "dynamic-5e7":
+        raise SystemExit("--tuning applies to the static workloads")
+    if args.cover < 0:
+        raise SystemExit("--tuning needs --cover 0, 1 or 2")
+    parts = args.tuning.split(",")
+    if len(parts) != 3 or not all(p.strip().isdigit() for p in parts):
+        raise SystemExit("--tuning takes CHUNK,BATCH,QBATCH (three integers)")
+    return tuple(int(p) for p in parts)
 
 
 def dist_env():
@@ -375,10 +393,9 @@ class StaticBench:
         # size the output once (the total is the same for every step) and let the autotuner
         # pick the cover, the scan's chunk size and work-queue batches for this shape
         self.ix = sfc.sfc_build3(self.pts, **opts) if self.dim == 3 else sfc.sfc_build(self.pts, self.curve, **opts)
-        if args.tuning:
-            if args.cover < 0:
-                raise SystemExit("--tuning needs --cover 0, 1 or 2")
-            chunk, batch, qbatch = (int(x) for x in args.tuning.split(","))
+        pinned = pinned_tuning(args)
+        if pinned:
+            chunk, batch, qbatch = pinned
             sfc.sfc_set_tuning(self.ix, chunk, batch, qbatch)
             self.tuned = {"chunk": chunk, "batch": batch, "qbatch": qbatch, "cover": sfc.sfc_cover_refine(self.ix),
                           "pinned": True}

@@ -109,3 +109,16 @@ def test_default_workload_is_the_learned_bounds_configuration():
     a = bench.parse([])
     assert a.workload == "mixed-1e8" and a.steps >= 10 and a.warmup >= 3
     assert bench.instance_seed(0) == 4 and bench.instance_seed(1) != 4
+
+
+def test_tuning_flag():
+    """--tuning CHUNK,BATCH,QBATCH pins the scan settings (with an explicit cover); malformed or
+    misplaced uses are refused while parsing, before any work."""
+    assert bench.pinned_tuning(bench.parse(["--tuning", "4096,16,2", "--cover", "1"])) == (4096, 16, 2)
+    assert bench.pinned_tuning(bench.parse([])) is None
+    for argv in (["--tuning", "4096,16,2"],                      # the autotuner would pick the cover
+                 ["--tuning", "4096,16", "--cover", "1"],
+                 ["--tuning", "4096,16,x", "--cover", "1"],
+                 ["--tuning", "4096,16,2", "--cover", "1", "--workload", "dynamic-5e7"]):
+        with pytest.raises(SystemExit):
+            bench.parse(argv)
